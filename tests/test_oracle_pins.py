@@ -1,0 +1,462 @@
+"""Pins of the FP64 CPU oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: exactness on
+polynomial data, closed forms, invariants of the scheme, an independent numpy
+solve of the least-squares problems, brute force on tiny meshes, the exact
+translating vortex, and the paper's observed convergence orders."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_10809_b300 import inputs as I
+
+GL = 0.28867513459481288225  # sqrt(3)/6
+
+
+# ---------------------------------------------------------------- helpers
+def interior_cells(nbr, rings=2):
+    """Cells whose `rings`-ring neighbourhood contains no boundary cell."""
+    bad = np.any(nbr < 0, axis=1)
+    for _ in range(rings):
+        grow = bad.copy()
+        for j in range(3):
+            nb = nbr[:, j]
+            ok = nb >= 0
+            grow[ok] |= bad[nb[ok]]
+        bad = grow
+    return np.nonzero(~bad)[0]
+
+
+def quad_fn(q):
+    def f(x, y):
+        return (q[0] + q[1] * x + q[2] * y + q[3] * x * x + q[4] * x * y + q[5] * y * y)[None]
+    return f
+
+
+def quad_jet(q, x, y):
+    return np.array([q[0] + q[1] * x + q[2] * y + q[3] * x * x + q[4] * x * y + q[5] * y * y,
+                     q[1] + 2 * q[3] * x + q[4] * y, q[2] + q[4] * x + 2 * q[5] * y,
+                     2 * q[3] + 0 * x, q[4] + 0 * x, 2 * q[5] + 0 * x])
+
+
+# ---------------------------------------------------------------- constants
+def test_linear_weights_are_the_papers_and_sum_to_one(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "paper_constants.json")))
+    gl = g["linear_weights"]["value"]
+    o = oracle.Oracle(I.structured_periodic(4, 1.0))
+    assert list(o._gl) == gl
+    # Eq. pxy is an identity only when the linear weights sum to one
+    assert abs(sum(gl) - 1.0) < 1e-15
+
+
+def test_pxy_identity_linear_weights_give_p1():
+    """Eq. pxy: with the nonlinear weights replaced by the linear ones, the
+    combination of Eq. recon is p1 itself, for any data."""
+    mesh = I.jittered_periodic(6, 1.0, seed=11)
+    rng = np.random.default_rng(0)
+    U = rng.normal(size=(3, 1, mesh.nt))
+    o = oracle.Oracle(mesh, linear_only=True)
+    for cell in (0, 17, 40):
+        r = o.reconstruct_cell(U, cell)
+        np.testing.assert_allclose(r["recon"], r["polys"][0], rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(r["omega"], [0.94, 0.02, 0.02, 0.02], rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- reconstruction
+def test_p1_reproduces_quadratics_and_p2_p4_linears():
+    mesh = I.jittered_box(7, 1.0, seed=3)
+    o = oracle.Oracle(mesh)
+    nbr, _ = o.neighbors()
+    rng = np.random.default_rng(1)
+    q = rng.normal(size=6)
+    U = I.initial_state(mesh, quad_fn(q), 1)
+    for cell in interior_cells(nbr, rings=0)[:12]:
+        r = o.reconstruct_cell(U, int(cell))
+        gp = r["gp"]
+        exact = quad_jet(q, gp[:, 0], gp[:, 1]).T      # [6 points, 6 derivs]
+        np.testing.assert_allclose(r["polys"][0], exact, rtol=1e-10, atol=1e-10)
+    ql = np.array([q[0], q[1], q[2], 0, 0, 0])
+    U = I.initial_state(mesh, quad_fn(ql), 1)
+    for cell in interior_cells(nbr, rings=0)[:12]:
+        r = o.reconstruct_cell(U, int(cell))
+        gp = r["gp"]
+        exact = quad_jet(ql, gp[:, 0], gp[:, 1]).T
+        for l in range(4):
+            np.testing.assert_allclose(r["polys"][l], exact, rtol=1e-10, atol=1e-10)
+        # linear data: all indicators equal, kappa = 0, omega = gamma, exact
+        np.testing.assert_allclose(r["beta"], r["beta"][0], rtol=1e-9)
+        np.testing.assert_allclose(r["omega"], [0.94, 0.02, 0.02, 0.02], rtol=1e-9)
+        np.testing.assert_allclose(r["recon"], exact, rtol=1e-10, atol=1e-10)
+
+
+def _numpy_p1(mesh, U, cell, nbr):
+    """Independent solve of Step 1 by the null-space method (scipy), with cell
+    means from a collapsed Gauss rule instead of edge midpoints."""
+    from scipy.linalg import null_space
+    P = mesh.unwrapped()
+    u, v, wt = I._tri_rule(5)
+
+    def pts(T):
+        return (T[0][None] + u[:, None] * (T[1] - T[0])[None] + v[:, None] * (T[2] - T[0])[None])
+
+    T0 = P[cell]
+    A = lambda T: 0.5 * ((T[1, 0] - T[0, 0]) * (T[2, 1] - T[0, 1]) - (T[2, 0] - T[0, 0]) * (T[1, 1] - T[0, 1]))
+    A0 = A(T0); h0 = np.sqrt(A0); c0 = T0.mean(axis=0)
+    X0 = (pts(T0) - c0) / h0
+    M = [(wt * X0[:, 0] ** 2).sum(), (wt * X0[:, 0] * X0[:, 1]).sum(), (wt * X0[:, 1] ** 2).sum()]
+
+    def phis(X):   # phi_1..phi_5 at points X [q, 2]
+        xi, et = X[:, 0], X[:, 1]
+        return np.stack([xi, et, xi * xi - M[0], xi * et - M[1], et * et - M[2]], axis=1)
+
+    def dphis(X):  # d/dxi and d/deta of phi_1..phi_5
+        xi, et = X[:, 0], X[:, 1]
+        z, o = 0 * xi, 1 + 0 * xi
+        return (np.stack([o, z, 2 * xi, et, z], axis=1), np.stack([z, o, z, xi, 2 * et], axis=1))
+
+    Cm, e, B, d = [], [], [], []
+    for j in range(3):
+        nb = nbr[cell, j]
+        Tn = P[nb]
+        Xn = (pts(Tn) - c0) / h0
+        An = A(Tn)
+        Cm.append((wt[:, None] * phis(Xn)).sum(0))
+        e.append(U[0, 0, nb] - U[0, 0, cell])
+        dx0, dy0 = dphis(X0); dxn, dyn = dphis(Xn)
+        B.append((An * (wt[:, None] * dxn).sum(0) + A0 * (wt[:, None] * dx0).sum(0)) / (An + A0))
+        B.append((An * (wt[:, None] * dyn).sum(0) + A0 * (wt[:, None] * dy0).sum(0)) / (An + A0))
+        d.append(h0 * (An * U[1, 0, nb] + A0 * U[1, 0, cell]) / (An + A0))
+        d.append(h0 * (An * U[2, 0, nb] + A0 * U[2, 0, cell]) / (An + A0))
+    Cm, e, B, d = map(np.array, (Cm, e, B, d))
+    cp = np.linalg.lstsq(Cm, e, rcond=None)[0]
+    N = null_space(Cm)
+    z = np.linalg.lstsq(B @ N, d - B @ cp, rcond=None)[0]
+    c = cp + N @ z
+    return c, c0, h0, M
+
+
+def test_p1_constrained_least_squares_matches_independent_solve():
+    mesh = I.jittered_box(6, 1.0, seed=5)
+    o = oracle.Oracle(mesh)
+    nbr, _ = o.neighbors()
+    rng = np.random.default_rng(2)
+    U = rng.normal(size=(3, 1, mesh.nt))    # inconsistent data: the LS part matters
+    for cell in interior_cells(nbr, rings=0)[:8]:
+        cell = int(cell)
+        r = o.reconstruct_cell(U, cell)
+        c, c0, h0, M = _numpy_p1(mesh, U, cell, nbr)
+        gp = r["gp"]
+        xi = (gp[:, 0] - c0[0]) / h0; et = (gp[:, 1] - c0[1]) / h0
+        val = U[0, 0, cell] + c[0] * xi + c[1] * et + c[2] * (xi * xi - M[0]) + c[3] * (xi * et - M[1]) + c[4] * (et * et - M[2])
+        px = (c[0] + 2 * c[2] * xi + c[3] * et) / h0
+        np.testing.assert_allclose(r["polys"][0][:, 0], val, rtol=1e-10, atol=1e-10)
+        np.testing.assert_allclose(r["polys"][0][:, 1], px, rtol=1e-10, atol=1e-10)
+        # the equality constraints (cell averages on K1..K3) hold exactly
+        # (checked through the independent solution having the same values)
+
+
+def test_smoothness_indicators_formula_on_quadratic():
+    """Eq. smoo1 for p1 = Q: |K0| (Qx^2 + Qy^2) + |K0|^2 (Qxx^2 + Qxy^2 + Qyy^2) at the barycenter."""
+    mesh = I.jittered_box(6, 1.0, seed=8)
+    o = oracle.Oracle(mesh)
+    nbr, _ = o.neighbors()
+    geo = o.cell_geometry()
+    q = np.array([0.3, -1.1, 0.7, 2.0, -0.5, 1.3])
+    U = I.initial_state(mesh, quad_fn(q), 1)
+    cell = int(interior_cells(nbr, rings=0)[3])
+    r = o.reconstruct_cell(U, cell)
+    a = geo["area"][cell]; x, y = geo["cx"][cell], geo["cy"][cell]
+    J = quad_jet(q, x, y)
+    b1 = a * (J[1] ** 2 + J[2] ** 2) + a * a * (J[3] ** 2 + J[4] ** 2 + J[5] ** 2)
+    assert abs(r["beta"][0] - b1) < 1e-10 * b1
+
+
+def test_nonlinear_weights_switch_off_p1_at_a_jump():
+    mesh = I.jittered_box(10, 1.0, seed=4)
+    fn = lambda x, y: (1.0 + (x > 0.5))[None] * 1.0
+    U = I.initial_state(mesh, fn, 1)
+    o = oracle.Oracle(mesh)
+    nbr, _ = o.neighbors()
+    geo = o.cell_geometry()
+    # a cell cut by the jump vs a cell far from it
+    near = int(np.argmin(np.abs(geo["cx"] - 0.5) + np.abs(geo["cy"] - 0.5)))
+    far = int(np.argmin(np.abs(geo["cx"] - 0.2) + np.abs(geo["cy"] - 0.5)))
+    rn = o.reconstruct_cell(U, near)
+    rf = o.reconstruct_cell(U, far)
+    assert rn["omega"][0] < 0.05 * 0.94
+    np.testing.assert_allclose(rf["omega"], [0.94, 0.02, 0.02, 0.02], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- Lax-Wendroff
+def test_lw_advection_closed_form():
+    rng = np.random.default_rng(3)
+    a = (0.7, -1.3)
+    for _ in range(5):
+        J = rng.normal(size=(6, 1))
+        out = oracle.lax_wendroff("advection", J, a=a)
+        W, Wx, Wy, Wxx, Wxy, Wyy = J[:, 0]
+        Wt = -(a[0] * Wx + a[1] * Wy)
+        Wtx = -(a[0] * Wxx + a[1] * Wxy)
+        Wty = -(a[0] * Wxy + a[1] * Wyy)
+        Wtt = a[0] ** 2 * Wxx + 2 * a[0] * a[1] * Wxy + a[1] ** 2 * Wyy
+        np.testing.assert_allclose(out[:, 0], [Wt, Wtx, Wty, Wtt], rtol=1e-14, atol=1e-14)
+
+
+def test_lw_burgers_closed_form():
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        J = rng.normal(size=(6, 1))
+        out = oracle.lax_wendroff("burgers", J)
+        W, Wx, Wy, Wxx, Wxy, Wyy = J[:, 0]
+        s = Wx + Wy
+        Wt = -W * s
+        Wtx = -(Wx * s + W * (Wxx + Wxy))
+        Wty = -(Wy * s + W * (Wxy + Wyy))
+        Wtt = -(Wt * s + W * (Wtx + Wty))
+        np.testing.assert_allclose(out[:, 0], [Wt, Wtx, Wty, Wtt], rtol=1e-13, atol=1e-13)
+
+
+def euler_jacobians(W, g=1.4):
+    """Textbook flux Jacobians of the 2D Euler equations."""
+    rho, m, n, E = W
+    u, v = m / rho, n / rho
+    q2 = u * u + v * v
+    p = (g - 1) * (E - 0.5 * rho * q2)
+    H = (E + p) / rho
+    A = np.array([[0, 1, 0, 0],
+                  [-u * u + 0.5 * (g - 1) * q2, (3 - g) * u, -(g - 1) * v, g - 1],
+                  [-u * v, v, u, 0],
+                  [u * (0.5 * (g - 1) * q2 - H), H - (g - 1) * u * u, -(g - 1) * u * v, g * u]])
+    B = np.array([[0, 0, 1, 0],
+                  [-u * v, v, u, 0],
+                  [-v * v + 0.5 * (g - 1) * q2, -(g - 1) * u, (3 - g) * v, g - 1],
+                  [v * (0.5 * (g - 1) * q2 - H), -(g - 1) * u * v, H - (g - 1) * v * v, g * v]])
+    return A, B
+
+
+def test_euler_flux_jacobian_matches_textbook_and_hessian_matches_fd():
+    rng = np.random.default_rng(5)
+    W = I.euler_from_primitive(np.array(1.2), np.array(0.3), np.array(-0.8), np.array(0.9))
+    for _ in range(4):
+        a = rng.normal(size=4); b = rng.normal(size=4)
+        out = oracle.flux_derivs("euler", W, a, b)
+        A, B = euler_jacobians(W)
+        np.testing.assert_allclose(out[0], A @ a, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(out[1], A @ b, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(out[3], B @ a, rtol=1e-13, atol=1e-13)
+        h = 1e-5
+        Ap, Bp = euler_jacobians(W + h * b); Am, Bm = euler_jacobians(W - h * b)
+        np.testing.assert_allclose(out[2], (Ap - Am) @ a / (2 * h), rtol=1e-7, atol=1e-8)
+        np.testing.assert_allclose(out[5], (Bp - Bm) @ a / (2 * h), rtol=1e-7, atol=1e-8)
+
+
+def _fd_jet(fn, x, y, h=2e-3):
+    """Value and derivatives up to second order by 4th-order central differences."""
+    c1 = np.array([1, -8, 0, 8, -1]) / (12 * h)
+    c2 = np.array([-1, 16, -30, 16, -1]) / (12 * h * h)
+    s = np.arange(-2, 3) * h
+    F = np.array([[fn(x + a, y + b) for b in s] for a in s])   # [5, 5, m]
+    W = F[2, 2]
+    Wx = np.tensordot(c1, F[:, 2], axes=1); Wy = np.tensordot(c1, F[2, :], axes=1)
+    Wxx = np.tensordot(c2, F[:, 2], axes=1); Wyy = np.tensordot(c2, F[2, :], axes=1)
+    Wxy = np.einsum("i,j,ijm->m", c1, c1, F)
+    return np.stack([W, Wx, Wy, Wxx, Wxy, Wyy])
+
+
+def test_lw_euler_reproduces_translating_vortex():
+    """The isentropic vortex translates with velocity (1, 1): W_t = -(W_x + W_y)
+    and W_tt = W_xx + 2 W_xy + W_yy hold exactly, so the Lax-Wendroff procedure
+    fed with the exact spatial jet must return them."""
+    fn = lambda x, y: I.vortex(np.array(x), np.array(y))
+    for (x, y) in ((5.7, 4.6), (4.2, 5.9), (6.1, 6.3)):
+        J = _fd_jet(fn, x, y)
+        out = oracle.lax_wendroff("euler", J)
+        Wt = -(J[1] + J[2]); Wtt = J[3] + 2 * J[4] + J[5]
+        Wtx = -(J[3] + J[4]); Wty = -(J[4] + J[5])
+        np.testing.assert_allclose(out[0], Wt, rtol=0, atol=2e-9)
+        np.testing.assert_allclose(out[1], Wtx, rtol=0, atol=1e-7)
+        np.testing.assert_allclose(out[2], Wty, rtol=0, atol=1e-7)
+        np.testing.assert_allclose(out[3], Wtt, rtol=0, atol=1e-7)
+
+
+# ---------------------------------------------------------------- whole step
+def test_step_exact_for_advected_quadratic_with_linear_weights():
+    """Quadratic data + linear weights: the reconstruction is exact, the
+    second-order Taylor expansion in time is exact, the Lobatto rule is exact for
+    the quadratic time dependence and two Gauss points are exact on the edges,
+    so one step reproduces the exact cell averages of W, W_x, W_y (Eqs. flx,
+    derave2d2) away from the boundary."""
+    mesh = I.jittered_box(9, 1.0, seed=6)
+    q = np.array([0.4, 0.9, -0.6, 1.1, 0.8, -0.7])
+    a = (0.8, -0.5)
+    o = oracle.Oracle(mesh, "advection", a=a, linear_only=True)
+    nbr, _ = o.neighbors()
+    U = I.initial_state(mesh, quad_fn(q), 1)
+    dt = 0.04
+    Un = o.step(U, dt)
+    shifted = lambda x, y: quad_fn(q)(x - a[0] * dt, y - a[1] * dt)
+    Ue = I.initial_state(mesh, shifted, 1)
+    cells = interior_cells(nbr, rings=2)
+    assert cells.size > 20
+    np.testing.assert_allclose(Un[:, :, cells], Ue[:, :, cells], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
+def test_conservation_on_periodic_mesh(eq):
+    mesh = I.jittered_periodic(8, 10.0 if eq == "euler" else 2.0, seed=12)
+    m = 4 if eq == "euler" else 1
+    fn = I.vortex if eq == "euler" else (I.advection_sine if eq == "advection" else I.burgers_sine)
+    U = I.initial_state(mesh, fn, m)
+    o = oracle.Oracle(mesh, eq)
+    area = o.cell_geometry()["area"]
+    s0 = (U[0] * area).sum(axis=1)
+    for _ in range(4):
+        U = o.step(U, 0.5 * o.cfl_dt(U))
+    s1 = (U[0] * area).sum(axis=1)
+    np.testing.assert_allclose(s1, s0, rtol=1e-13)
+    scale = (np.abs(U[1]) * area).sum(axis=1) + (np.abs(U[2]) * area).sum(axis=1)
+    assert np.all(np.abs((U[1] * area).sum(axis=1)) < 1e-13 * scale)
+    assert np.all(np.abs((U[2] * area).sum(axis=1)) < 1e-13 * scale)
+
+
+@pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
+@pytest.mark.parametrize("kind", ["jittered", "poisson", "box"])
+def test_free_stream_preserved(eq, kind):
+    if kind == "jittered":
+        mesh = I.jittered_periodic(7, 1.0, seed=21)
+    elif kind == "poisson":
+        mesh = I.poisson_delaunay_periodic(1.0, 150, seed=22)
+    else:
+        mesh = I.jittered_box(7, 1.0, seed=23)
+    m = 4 if eq == "euler" else 1
+    const = {"advection": [2.5], "burgers": [0.7], "euler": list(I.euler_from_primitive(1.3, 0.4, -0.7, 0.9))}[eq]
+    U = np.zeros((3, m, mesh.nt)); U[0] = np.array(const)[:, None]
+    o = oracle.Oracle(mesh, eq)
+    U1 = U
+    for _ in range(3):
+        U1 = o.step(U1, o.cfl_dt(U1))
+    np.testing.assert_allclose(U1[0], U[0], rtol=2e-14)
+    assert np.abs(U1[1:]).max() < 1e-12
+
+
+def test_connectivity_matches_brute_force():
+    for mesh in (I.jittered_periodic(4, 1.0, seed=1), I.jittered_box(4, seed=2),
+                 I.poisson_delaunay_periodic(1.0, 40, seed=3)):
+        o = oracle.Oracle(mesh)
+        nbr, nbe = o.neighbors()
+        T = mesh.tri
+        for t in range(mesh.nt):
+            for j in range(3):
+                a, b = T[t, j], T[t, (j + 1) % 3]
+                hits = [(u, k) for u in range(mesh.nt) for k in range(3)
+                        if u != t and {T[u, k], T[u, (k + 1) % 3]} == {a, b}]
+                if hits:
+                    assert len(hits) == 1
+                    assert (nbr[t, j], nbe[t, j]) == hits[0]
+                else:
+                    assert nbr[t, j] == -1 and mesh.bc == 1
+
+
+def test_dual_numbers_give_the_directional_derivative():
+    mesh = I.jittered_periodic(4, 10.0, seed=31)
+    U0 = I.initial_state(mesh, I.vortex, 4)
+    rng = np.random.default_rng(7)
+    dU = rng.normal(size=U0.shape) * np.abs(U0).mean(axis=2, keepdims=True) * 0.1
+    o = oracle.Oracle(mesh, "euler")
+    dts = [0.05, 0.05, 0.04]
+    U1, dU1 = o.run_dual(U0, dU, dts)
+    np.testing.assert_allclose(U1, o.run_dts(U0, dts), rtol=1e-15, atol=1e-15)
+    h = 1e-6
+    fd = (o.run_dts(U0 + h * dU, dts) - o.run_dts(U0 - h * dU, dts)) / (2 * h)
+    assert np.abs(fd - dU1).max() < 1e-6 * np.abs(dU1).max()
+
+
+# ---------------------------------------------------------------- convergence
+def _orders(errs):
+    return [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+def test_third_order_on_smooth_advection(golden_dir):
+    errs = []
+    for n in (10, 20, 40, 80):
+        mesh = I.config1_mesh(n)
+        U0 = I.initial_state(mesh, I.advection_sine, 1)
+        U, _ = oracle.Oracle(mesh, "advection").run_to(U0, 0.5)
+        We = I.cell_averages(mesh, lambda x, y: I.advection_sine(x - 0.5, y - 0.5), 1)[0]
+        errs.append(I.error_norms(mesh, U[0, 0], We)[0])
+    paper = json.load(open(os.path.join(golden_dir, "paper_convergence.json")))
+    fine = min(min(v["order"][-2:]) for k, v in paper.items() if not k.startswith("_"))
+    o = _orders(errs)
+    assert o[-1] > fine - 0.1 and o[-1] < 3.3, (errs, o)
+
+
+def test_burgers_and_vortex_converge():
+    T = 0.5 / np.pi
+    errs = []
+    for n in (10, 20, 40):
+        mesh = I.jittered_periodic(n, 4.0, 0.15, seed=2)
+        U0 = I.initial_state(mesh, I.burgers_sine, 1)
+        U, _ = oracle.Oracle(mesh, "burgers").run_to(U0, T)
+        We = I.cell_averages(mesh, lambda x, y: I.burgers_exact(x, y, T), 1)[0]
+        errs.append(I.error_norms(mesh, U[0, 0], We)[0])
+    assert min(_orders(errs)) > 2.5, errs
+    errs = []
+    for n in (10, 20, 40):
+        mesh = I.jittered_periodic(n, 10.0, 0.15, seed=5)
+        U0 = I.initial_state(mesh, I.vortex, 4)
+        U, _ = oracle.Oracle(mesh, "euler").run_to(U0, 1.0)
+        We = I.cell_averages(mesh, lambda x, y: I.vortex(x, y, 1.0), 4)[0]
+        errs.append(I.error_norms(mesh, U[0, 0], We)[0])
+    o = _orders(errs)
+    # the paper's vortex orders rise from about 2 to 3 over the same range
+    assert o[0] > 1.8 and o[1] > 2.3, (errs, o)
+
+
+# ---------------------------------------------------------------- invariances
+@pytest.mark.parametrize("eq", ["burgers", "euler"])
+def test_step_independent_of_numbering(eq):
+    """The scheme does not depend on how cells are numbered or which vertex
+    comes first: reversing the cell order and rotating every triangle's vertex
+    list must give the same step (this fixes the symmetric roles of the
+    interior and exterior sides in Eq. timeflux and of K1, K2, K3 in Eq.
+    nonlinearweight)."""
+    L = 10.0 if eq == "euler" else 4.0
+    mesh = I.jittered_periodic(6, L, seed=41)
+    m = 4 if eq == "euler" else 1
+    rng = np.random.default_rng(9)
+    fn = I.vortex if eq == "euler" else I.burgers_sine
+    U = I.initial_state(mesh, fn, m)
+    U[0] *= 1 + 0.05 * rng.random(U[0].shape)     # make the data rough
+    perm = np.arange(mesh.nt)[::-1]
+    rot = rng.integers(0, 3, mesh.nt)
+    tri2 = np.array([np.roll(t, -r) for t, r in zip(mesh.tri[perm], rot[perm])], dtype=np.int32)
+    mesh2 = I.Mesh(mesh.xy, tri2, mesh.Lx, mesh.Ly, mesh.bc)
+    dt = 0.02
+    A = oracle.Oracle(mesh, eq).step(U, dt)
+    B = oracle.Oracle(mesh2, eq).step(U[:, :, perm], dt)
+    np.testing.assert_allclose(B, A[:, :, perm], rtol=1e-12, atol=1e-12 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("eq", ["advection", "euler"])
+def test_step_invariant_under_scaling_of_space_and_time(eq):
+    """x -> s x, t -> s t leaves the conservation law unchanged; the scheme
+    (dimensionless least-squares rows, |K0|^|s| in Eq. smoo1, dimensionless
+    weights) must then map cell averages of W to themselves and derivative
+    averages to 1/s times themselves."""
+    s = 3.7
+    mesh = I.jittered_periodic(6, 10.0, seed=43)
+    mesh_s = I.Mesh(mesh.xy * s, mesh.tri, mesh.Lx * s, mesh.Ly * s, mesh.bc)
+    m = 4 if eq == "euler" else 1
+    fn = I.vortex if eq == "euler" else (lambda x, y: I.advection_sine(x / 5, y / 5))
+    U = I.initial_state(mesh, fn, m)
+    rng = np.random.default_rng(10)
+    U[0] *= 1 + 0.05 * rng.random(U[0].shape)
+    Us = U.copy(); Us[1:] /= s
+    dt = 0.03
+    A = oracle.Oracle(mesh, eq).step(U, dt)
+    B = oracle.Oracle(mesh_s, eq).step(Us, dt * s)
+    np.testing.assert_allclose(B[0], A[0], rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(B[1:] * s, A[1:], rtol=1e-10, atol=1e-10 * np.abs(A[1:]).max())
