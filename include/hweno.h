@@ -1,0 +1,143 @@
+/*
+ * hweno.h -- C ABI of the B300 library for the compact simple HWENO scheme
+ * with ADER time discretization on triangular meshes (Luo, Zhao, Qiu, Chen).
+ *
+ * One time step (Section 2) does, over every triangle and every edge:
+ *   1. one HWENO reconstruction per cell from the cell averages of W, W_x, W_y
+ *      on the compact stencil {K0, K1, K2, K3} (Section 2.2, Steps 1-6,
+ *      Eqs. aver, pxy, smoo1, nonlinearweight, recon);
+ *   2. the Lax-Wendroff procedure at the two Gauss points of every edge and the
+ *      time Taylor expansion on each side (Section 2.1, Eqs. tay, tayext),
+ *      followed by the local Lax-Friedrichs flux at the Gauss-Lobatto time nodes
+ *      (Eqs. fx, flux);
+ *   3. the finite-volume update of the cell averages (Eq. flx) and the
+ *      Green-Gauss update of the derivative averages from the central edge
+ *      values at t_{n+1} (Eqs. derave2d1, derave2d2, timeflux, taylor2dtime).
+ *
+ * Conventions shared by every entry point
+ *   - Host state arrays are double, structure-of-arrays, in the caller's cell
+ *     numbering: Wbar[c*ntri + i] is the average of component c of W over
+ *     triangle i, Vbar / Ybar the averages of W_x / W_y (Eq. aver).
+ *     Components: 1 for advection and Burgers, 4 (rho, rho u, rho v, E) for Euler.
+ *   - The library renumbers cells internally along a Hilbert curve; this never
+ *     shows through the interface.
+ *   - Device memory is owned by the caller: hw_state_init receives a workspace
+ *     pointer of at least hw_workspace_bytes() bytes (for instance a torch
+ *     uint8 CUDA tensor) and the library never frees it.  The library allocates
+ *     no device memory of its own; it owns only the opaque host handles.
+ *   - All device work is enqueued on the caller's CUDA stream.
+ *   - Every function returns an hw_status; nothing else crosses the ABI on
+ *     failure.  hw_last_error() gives a message for the calling thread.
+ *     Device-side conditions (non-finite values, non-positive density or
+ *     pressure, a spin limit reached) are latched in a device flag and
+ *     reported by the next synchronising call (hw_run_to, hw_get_state,
+ *     hw_status_flags).
+ */
+#ifndef HWENO_H_
+#define HWENO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HW_OK = 0,
+  HW_EINVAL = 1,      /* bad argument */
+  HW_ENOMEM = 2,      /* workspace too small / host allocation failed */
+  HW_ECUDA = 3,       /* a CUDA runtime call failed */
+  HW_EMESH = 4,       /* non-manifold, inverted or degenerate mesh, ill-conditioned stencil */
+  HW_ENONFINITE = 5,  /* NaN/Inf in the state, or rho <= 0 / p <= 0 (Euler) */
+  HW_ETIMEOUT = 6,    /* a bounded device spin gave up */
+  HW_ESTATE = 7       /* call not valid in the object's current state */
+} hw_status;
+
+typedef enum { HW_ADVECTION = 0, HW_BURGERS = 1, HW_EULER = 2 } hw_equation;
+typedef enum { HW_FP64 = 0, HW_FP32 = 1 } hw_precision;
+typedef enum { HW_BC_PERIODIC = 0, HW_BC_TRANSMISSIVE = 1 } hw_bc;
+
+/* Solver options.  Defaults (hw_options_default): the paper's constants --
+ * linear weights 0.94, 0.02, 0.02, 0.02 (Section 2.2, Step 3), epsilon 1e-8
+ * (Step 5), CFL 0.5 (Section 3), gamma 1.4 (Example 3.2). */
+typedef struct {
+  int32_t eq;           /* hw_equation */
+  int32_t reserved0;
+  double ax, ay;        /* advection velocity (HW_ADVECTION) */
+  double gamma_gas;     /* ratio of specific heats (HW_EULER) */
+  double cfl;           /* dt = cfl * min_K inradius_K / lambda_K */
+  double gamma_lin[4];  /* linear weights gamma_1..gamma_4, sum 1 */
+  double eps;           /* epsilon in the nonlinear weights */
+} hw_options;
+
+typedef struct hw_mesh hw_mesh;
+typedef struct hw_solver hw_solver;
+
+void hw_options_default(hw_options* opt);
+
+/* Build the mesh and its FP64 precompute (connectivity, stencils, per-cell
+ * reconstruction operators for Steps 1-2 of Section 2.2, edge normals and
+ * Gauss points) on the host.
+ *   xy   : [nvert*2] vertex coordinates (x, y), host, read only
+ *   tri  : [ntri*3] vertex indices, counter-clockwise, host, read only
+ *   Lx,Ly: period in x / y (0 = not periodic); a periodic mesh lists each
+ *          vertex once and triangles refer to vertices modulo the period
+ *   bc   : hw_bc; HW_BC_PERIODIC requires every edge to have two triangles
+ * Errors: HW_EINVAL (null pointers, indices out of range), HW_EMESH. */
+hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, int64_t ntri, double Lx, double Ly,
+                         int32_t bc, hw_mesh** out);
+hw_status hw_mesh_destroy(hw_mesh* mesh);
+/* Number of triangles. */
+int64_t hw_mesh_ntri(const hw_mesh* mesh);
+/* Neighbour across local edge j (from vertex j to vertex j+1) of triangle i,
+ * caller's numbering, -1 on a boundary: nbr[3*i + j].  nbe (optional, may be
+ * NULL) receives the neighbour's local index of the same edge. Host arrays. */
+hw_status hw_mesh_neighbors(const hw_mesh* mesh, int32_t* nbr, int32_t* nbe);
+/* Internal (Hilbert) order: perm[k] = caller's index of the k-th cell. */
+hw_status hw_mesh_permutation(const hw_mesh* mesh, int32_t* perm);
+
+/* Bytes of device workspace hw_state_init needs for this mesh / options /
+ * precision (geometry, two state buffers, edge-point buffer, staging). */
+hw_status hw_workspace_bytes(const hw_mesh* mesh, const hw_options* opt, int32_t precision, size_t* bytes);
+
+/* Upload geometry and the initial state (host arrays as described above) into
+ * the caller's workspace and compute the first CFL time step.  The workspace
+ * must stay valid until hw_solver_destroy.  cuda_stream: cudaStream_t (NULL =
+ * legacy default stream).  Synchronises the stream before returning. */
+hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t precision, const double* Wbar,
+                        const double* Vbar, const double* Ybar, void* workspace, size_t workspace_bytes,
+                        void* cuda_stream, hw_solver** out);
+/* Replace the state (host arrays) and set the time to t; recomputes the CFL
+ * step.  The copy is enqueued on the stream; the host arrays must stay valid
+ * until the stream reaches it (pinned memory gives a true asynchronous copy). */
+hw_status hw_set_state(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, double t);
+/* One time step, asynchronous on the stream.  dt > 0: that step size; dt <= 0:
+ * the CFL step held on the device (clipped to the target time of the last
+ * hw_run_to, if any). */
+hw_status hw_step(hw_solver* s, double dt);
+/* Advance to time T with CFL steps (last one clipped to hit T) through a
+ * captured CUDA graph of several steps; synchronises.  nsteps (may be NULL)
+ * receives the number of steps taken.  Returns HW_ENONFINITE if the state went
+ * non-finite / non-physical. */
+hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps);
+/* Copy the state back to host arrays in the caller's numbering and report the
+ * time; synchronises.  Any pointer may be NULL to skip it. */
+hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, double* t);
+/* Sum over cells of |K| * Wbar_K per component, accumulated in FP64 on the
+ * device in a fixed order (deterministic); sums[c], synchronises. */
+hw_status hw_conservation(hw_solver* s, double* sums);
+/* Device flags latched since the last call (bit 0: non-finite / non-physical
+ * state, bit 1: spin limit reached); clears them; synchronises. */
+hw_status hw_status_flags(hw_solver* s, uint32_t* flags);
+/* Current time, current device time step and steps taken; synchronises. */
+hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps);
+hw_status hw_solver_destroy(hw_solver* s);
+
+/* Message of the last failing call on this thread. */
+const char* hw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWENO_H_ */

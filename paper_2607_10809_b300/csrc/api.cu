@@ -1,0 +1,343 @@
+// C ABI of the HWENO library (declared in include/hweno.h): mesh handles,
+// caller-owned device workspace, state I/O in the caller's numbering, single
+// steps, and run_to through a captured CUDA graph of several steps.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hweno.h"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace hw;
+
+struct hw_mesh {
+  HostMesh M;
+};
+
+namespace {
+thread_local std::string g_last_error;
+
+hw_status fail(hw_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define HW_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(HW_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kGraphSteps = 16;  // steps per captured graph (even: the state parity is preserved)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t rgeo, igeo, U0, U1, Pb, area, perm, stage, sc, partial, consv, total;
+};
+
+Layout make_layout(int64_t N, int m, int prec) {
+  const size_t s = prec == HW_FP64 ? 8 : 4;
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  L.rgeo = take((size_t)NRGEO * N * s);
+  L.igeo = take((size_t)NIGEO * N * 4);
+  L.U0 = take((size_t)3 * m * N * s);
+  L.U1 = take((size_t)3 * m * N * s);
+  L.Pb = take((size_t)18 * m * N * s);
+  L.area = take((size_t)N * 8);
+  L.perm = take((size_t)N * 4);
+  L.stage = take((size_t)3 * m * N * 8);
+  L.sc = take(sizeof(DevScalars));
+  L.partial = take((size_t)kConsvBlocks * 4 * 8);
+  L.consv = take(4 * 8);
+  L.total = o;
+  return L;
+}
+
+int ncomp(int eq) { return eq == HW_EULER ? 4 : 1; }
+
+hw_status check_options(const hw_options* o) {
+  if (!o) return fail(HW_EINVAL, "options is NULL");
+  if (o->eq < 0 || o->eq > 2) return fail(HW_EINVAL, "unknown equation");
+  if (!(o->cfl > 0)) return fail(HW_EINVAL, "cfl must be positive");
+  if (o->eq == HW_EULER && !(o->gamma_gas > 1)) return fail(HW_EINVAL, "gamma_gas must exceed 1");
+  if (!(o->gamma_lin[0] > 0)) return fail(HW_EINVAL, "gamma_1 must be positive");
+  return HW_OK;
+}
+}  // namespace
+
+struct hw_solver {
+  hw_options opt;
+  int prec = 0, eq = 0, m = 1;
+  int64_t N = 0;
+  char* ws = nullptr;
+  Layout L{};
+  int cur = 0;  // index of the current state buffer
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  DevScalars* h_sc = nullptr;  // pinned mirror for readback
+  double* h_consv = nullptr;
+
+  void* U(int k) { return ws + (k == 0 ? L.U0 : L.U1); }
+  DevScalars* sc() { return reinterpret_cast<DevScalars*>(ws + L.sc); }
+  StepArgs args(int from, double dt_fixed) {
+    StepArgs a{};
+    a.rgeo = ws + L.rgeo;
+    a.igeo = reinterpret_cast<const int32_t*>(ws + L.igeo);
+    a.N = (int)N;
+    a.U = U(from);
+    a.Un = U(1 - from);
+    a.Pb = ws + L.Pb;
+    a.sc = sc();
+    a.dt_fixed = dt_fixed;
+    a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
+    for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
+    return a;
+  }
+};
+
+extern "C" {
+
+const char* hw_last_error(void) { return g_last_error.c_str(); }
+
+void hw_options_default(hw_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eq = HW_ADVECTION;
+  o->ax = 1.0; o->ay = 1.0;
+  o->gamma_gas = 1.4;
+  o->cfl = 0.5;
+  o->gamma_lin[0] = 0.94; o->gamma_lin[1] = 0.02; o->gamma_lin[2] = 0.02; o->gamma_lin[3] = 0.02;
+  o->eps = 1e-8;
+}
+
+hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, int64_t ntri, double Lx, double Ly,
+                         int32_t bc, hw_mesh** out) {
+  if (!xy || !tri || !out || nvert <= 0 || ntri <= 0) return fail(HW_EINVAL, "null pointer or empty mesh");
+  if (bc != HW_BC_PERIODIC && bc != HW_BC_TRANSMISSIVE) return fail(HW_EINVAL, "unknown boundary condition");
+  hw_mesh* h = new (std::nothrow) hw_mesh();
+  if (!h) return fail(HW_ENOMEM, "host allocation failed");
+  std::string err = build_mesh(xy, nvert, tri, ntri, Lx, Ly, bc, h->M);
+  if (!err.empty()) {
+    delete h;
+    const bool inval = err.find("out of range") != std::string::npos || err.find("needs") != std::string::npos;
+    return fail(inval ? HW_EINVAL : HW_EMESH, err);
+  }
+  *out = h;
+  return HW_OK;
+}
+
+hw_status hw_mesh_destroy(hw_mesh* mesh) {
+  delete mesh;
+  return HW_OK;
+}
+
+int64_t hw_mesh_ntri(const hw_mesh* mesh) { return mesh ? mesh->M.nt : -1; }
+
+hw_status hw_mesh_neighbors(const hw_mesh* mesh, int32_t* nbr, int32_t* nbe) {
+  if (!mesh || !nbr) return fail(HW_EINVAL, "null pointer");
+  std::memcpy(nbr, mesh->M.nbr_orig.data(), mesh->M.nbr_orig.size() * sizeof(int32_t));
+  if (nbe) std::memcpy(nbe, mesh->M.nbe_orig.data(), mesh->M.nbe_orig.size() * sizeof(int32_t));
+  return HW_OK;
+}
+
+hw_status hw_mesh_permutation(const hw_mesh* mesh, int32_t* perm) {
+  if (!mesh || !perm) return fail(HW_EINVAL, "null pointer");
+  std::memcpy(perm, mesh->M.perm.data(), mesh->M.perm.size() * sizeof(int32_t));
+  return HW_OK;
+}
+
+hw_status hw_workspace_bytes(const hw_mesh* mesh, const hw_options* opt, int32_t precision, size_t* bytes) {
+  if (!mesh || !bytes) return fail(HW_EINVAL, "null pointer");
+  if (hw_status s = check_options(opt)) return s;
+  if (precision != HW_FP64 && precision != HW_FP32) return fail(HW_EINVAL, "unknown precision");
+  *bytes = make_layout(mesh->M.nt, ncomp(opt->eq), precision).total;
+  return HW_OK;
+}
+
+static hw_status upload_state(hw_solver* s, const double* W, const double* V, const double* Y, double t) {
+  const size_t plane = (size_t)s->m * s->N * sizeof(double);
+  double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
+  HW_CUDA(cudaMemcpyAsync(stage, W, plane, cudaMemcpyHostToDevice, s->stream));
+  HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + plane, V, plane, cudaMemcpyHostToDevice, s->stream));
+  HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + 2 * plane, Y, plane, cudaMemcpyHostToDevice, s->stream));
+  launch_scatter(s->prec, stage, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, 3 * s->m,
+                 s->U(s->cur), s->stream);
+  launch_reset(s->sc(), t, s->opt.cfl, s->stream);
+  launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
+  HW_CUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t precision, const double* Wbar,
+                        const double* Vbar, const double* Ybar, void* workspace, size_t workspace_bytes,
+                        void* cuda_stream, hw_solver** out) {
+  if (!mesh || !Wbar || !Vbar || !Ybar || !workspace || !out) return fail(HW_EINVAL, "null pointer");
+  if (hw_status st = check_options(opt)) return st;
+  if (precision != HW_FP64 && precision != HW_FP32) return fail(HW_EINVAL, "unknown precision");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(HW_EINVAL, "workspace must be 256-byte aligned");
+  const HostMesh& M = mesh->M;
+  hw_solver* s = new (std::nothrow) hw_solver();
+  if (!s) return fail(HW_ENOMEM, "host allocation failed");
+  s->opt = *opt;
+  s->prec = precision;
+  s->eq = opt->eq;
+  s->m = ncomp(opt->eq);
+  s->N = M.nt;
+  s->L = make_layout(M.nt, s->m, precision);
+  if (workspace_bytes < s->L.total) { delete s; return fail(HW_ENOMEM, "workspace smaller than hw_workspace_bytes"); }
+  s->ws = static_cast<char*>(workspace);
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](hw_status st) { hw_solver_destroy(s); return st; };
+  if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&s->h_sc, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&s->h_consv, 4 * sizeof(double)) != cudaSuccess)
+    return bail(fail(HW_ECUDA, "stream / pinned host buffer creation failed"));
+  // geometry in the solver precision
+  const size_t nr = (size_t)NRGEO * M.nt;
+  cudaError_t e;
+  if (precision == HW_FP64) {
+    e = cudaMemcpyAsync(s->ws + s->L.rgeo, M.rgeo.data(), nr * 8, cudaMemcpyHostToDevice, s->stream);
+  } else {
+    std::vector<float> tmp(nr);
+    for (size_t k = 0; k < nr; ++k) tmp[k] = (float)M.rgeo[k];
+    e = cudaMemcpyAsync(s->ws + s->L.rgeo, tmp.data(), nr * 4, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->ws + s->L.igeo, M.igeo.data(), (size_t)NIGEO * M.nt * 4, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->ws + s->L.area, M.area.data(), (size_t)M.nt * 8, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->ws + s->L.perm, M.perm.data(), (size_t)M.nt * 4, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return bail(fail(HW_ECUDA, std::string("geometry upload: ") + cudaGetErrorString(e)));
+  s->cur = 0;
+  if (hw_status st = upload_state(s, Wbar, Vbar, Ybar, 0.0)) return bail(st);
+  if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+    return bail(fail(HW_ECUDA, std::string("state_init: ") + cudaGetErrorString(e)));
+  *out = s;
+  return HW_OK;
+}
+
+hw_status hw_set_state(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, double t) {
+  if (!s || !Wbar || !Vbar || !Ybar) return fail(HW_EINVAL, "null pointer");
+  return upload_state(s, Wbar, Vbar, Ybar, t);
+}
+
+hw_status hw_step(hw_solver* s, double dt) {
+  if (!s) return fail(HW_EINVAL, "null solver");
+  launch_step(s->prec, s->eq, s->args(s->cur, dt > 0 ? dt : 0.0), s->stream);
+  HW_CUDA(cudaGetLastError());
+  s->cur = 1 - s->cur;
+  return HW_OK;
+}
+
+static hw_status ensure_graph(hw_solver* s, int parity) {
+  if (s->graph[parity]) return HW_OK;
+  cudaGraph_t g = nullptr;
+  HW_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int cur = parity;
+  for (int k = 0; k < kGraphSteps; ++k) {
+    launch_step(s->prec, s->eq, s->args(cur, 0.0), s->cap_stream);
+    cur = 1 - cur;
+  }
+  cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+  if (e != cudaSuccess) return fail(HW_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&s->graph[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(HW_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return HW_OK;
+}
+
+hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps) {
+  if (!s) return fail(HW_EINVAL, "null solver");
+  if (!(T == T)) return fail(HW_EINVAL, "T is NaN");
+  HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  const long long n0 = s->h_sc->nsteps;
+  launch_set_target(s->sc(), T, 1, s->stream);
+  if (hw_status st = ensure_graph(s, s->cur)) return st;
+  for (long long iter = 0;; ++iter) {
+    HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
+    HW_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->h_sc->flags & 1u) {
+      if (nsteps) *nsteps = s->h_sc->nsteps - n0;
+      return fail(HW_ENONFINITE, "state became non-finite or non-physical");
+    }
+    if (s->h_sc->done) break;
+    if (!(s->h_sc->dt > 0) || iter > (1ll << 26))
+      return fail(HW_ESTATE, "time step vanished before reaching T");
+    HW_CUDA(cudaGraphLaunch(s->graph[s->cur], s->stream));
+  }
+  if (nsteps) *nsteps = s->h_sc->nsteps - n0;
+  return HW_OK;
+}
+
+hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, double* t) {
+  if (!s) return fail(HW_EINVAL, "null solver");
+  const size_t plane = (size_t)s->m * s->N * sizeof(double);
+  double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
+  launch_gather(s->prec, s->U(s->cur), reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, 3 * s->m,
+                stage, s->stream);
+  HW_CUDA(cudaGetLastError());
+  if (Wbar) HW_CUDA(cudaMemcpyAsync(Wbar, stage, plane, cudaMemcpyDeviceToHost, s->stream));
+  if (Vbar) HW_CUDA(cudaMemcpyAsync(Vbar, reinterpret_cast<char*>(stage) + plane, plane, cudaMemcpyDeviceToHost, s->stream));
+  if (Ybar) HW_CUDA(cudaMemcpyAsync(Ybar, reinterpret_cast<char*>(stage) + 2 * plane, plane, cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  if (t) *t = s->h_sc->t;
+  return HW_OK;
+}
+
+hw_status hw_conservation(hw_solver* s, double* sums) {
+  if (!s || !sums) return fail(HW_EINVAL, "null pointer");
+  double* partial = reinterpret_cast<double*>(s->ws + s->L.partial);
+  double* out = reinterpret_cast<double*>(s->ws + s->L.consv);
+  launch_consv(s->prec, s->U(s->cur), reinterpret_cast<const double*>(s->ws + s->L.area), (int)s->N, s->m, partial,
+               out, s->stream);
+  HW_CUDA(cudaGetLastError());
+  HW_CUDA(cudaMemcpyAsync(s->h_consv, out, s->m * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  for (int c = 0; c < s->m; ++c) sums[c] = s->h_consv[c];
+  return HW_OK;
+}
+
+hw_status hw_status_flags(hw_solver* s, uint32_t* flags) {
+  if (!s || !flags) return fail(HW_EINVAL, "null pointer");
+  HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  *flags = s->h_sc->flags;
+  HW_CUDA(cudaMemsetAsync(&s->sc()->flags, 0, sizeof(unsigned int), s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  return HW_OK;
+}
+
+hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps) {
+  if (!s) return fail(HW_EINVAL, "null solver");
+  HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  if (t) *t = s->h_sc->t;
+  if (dt) *dt = s->h_sc->dt;
+  if (nsteps) *nsteps = s->h_sc->nsteps;
+  return HW_OK;
+}
+
+hw_status hw_solver_destroy(hw_solver* s) {
+  if (!s) return HW_OK;
+  for (int p = 0; p < 2; ++p)
+    if (s->graph[p]) cudaGraphExecDestroy(s->graph[p]);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->h_sc) cudaFreeHost(s->h_sc);
+  if (s->h_consv) cudaFreeHost(s->h_consv);
+  delete s;
+  return HW_OK;
+}
+
+}  // extern "C"

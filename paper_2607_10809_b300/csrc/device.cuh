@@ -1,0 +1,307 @@
+// Device-side building blocks of the HWENO step: state/geometry views,
+// the per-cell reconstruction (Section 2.2), the Lax-Wendroff procedure
+// (Section 2.1) and the flux functions.  Included by the kernel files only.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace hw {
+
+// Device-resident scalars of one solve (time, step, target, flags).
+struct DevScalars {
+  double t;                          // current time
+  double dt;                         // step to take next (CFL, clipped)
+  double T;                          // target time when has_T
+  double cfl;
+  unsigned long long lam_min_bits;   // min_K inradius/lambda as the bits of a positive double
+  unsigned int counter;              // blocks done (last-block finalisation)
+  unsigned int flags;                // bit 0: non-finite / non-physical, bit 1: spin limit
+  long long nsteps;                  // steps taken
+  int done;                          // target reached
+  int has_T;
+  int pad[2];
+};
+
+struct EqParams {
+  double ax, ay, gam, eps;
+  double g[4];
+};
+
+template <typename R> struct GeoView {
+  const R* __restrict__ rg;        // [NRGEO][N]
+  const int32_t* __restrict__ ig;  // [NIGEO][N]
+  int N;
+  __device__ __forceinline__ R r(int p, int i) const { return __ldg(rg + (size_t)p * N + i); }
+  __device__ __forceinline__ int32_t n(int p, int i) const { return __ldg(ig + (size_t)p * N + i); }
+};
+
+constexpr int kEqAdvection = 0, kEqBurgers = 1, kEqEuler = 2;
+template <int EQ> struct EqTraits { static constexpr int m = (EQ == kEqEuler) ? 4 : 1; };
+
+__device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------- nonlinear weights
+// Step 5 (Eq. nonlinearweight) for one component; also returns nothing else.
+// In double the paper's expression is evaluated as written.
+__device__ __forceinline__ void nonlinear_weights(double Wave, const double beta[4], const double g[4], double eps,
+                                                  double om[4]) {
+  const double tau = fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]) + fabs(beta[0] - beta[3]);
+  const double kappa = tau * tau / 9.0;
+  const double W2 = Wave * Wave, W4 = W2 * W2;
+  double wb[4], s = 0.0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) { wb[l] = g[l] * (1.0 + kappa / (W4 * eps + W2 * beta[l])); s += wb[l]; }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) om[l] = wb[l] / s;
+}
+
+// Single precision: the same expression in float while W_ave^4 * eps stays a
+// normal float; below that (|W_ave| < 2^-20) the terms cannot be represented in
+// float and the expression is evaluated in double.  A non-finite sum falls back
+// to the linear weights.
+__device__ __forceinline__ void nonlinear_weights(float Wave, const float beta[4], const double g[4], double eps,
+                                                  float om[4]) {
+  if (fabsf(Wave) < 9.5367431640625e-07f) {
+    double bd[4] = {beta[0], beta[1], beta[2], beta[3]}, od[4];
+    nonlinear_weights((double)Wave, bd, g, eps, od);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) om[l] = (float)od[l];
+    return;
+  }
+  const float tau = fabsf(beta[0] - beta[1]) + fabsf(beta[0] - beta[2]) + fabsf(beta[0] - beta[3]);
+  const float kappa = tau * tau * (1.0f / 9.0f);
+  const float W2 = Wave * Wave, W4e = W2 * W2 * (float)eps;
+  float wb[4], s = 0.f;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) { wb[l] = (float)g[l] * (1.0f + kappa / (W4e + W2 * beta[l])); s += wb[l]; }
+  if (!isfinite(s) || s <= 0.f) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) om[l] = (float)g[l];
+    return;
+  }
+  const float is = 1.0f / s;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) om[l] = wb[l] * is;
+}
+
+// ---------------------------------------------------------------- reconstruction
+// Steps 1-6 of Section 2.2 for component c of cell i: returns the combined
+// quadratic (Eq. recon) as monomials in the scaled frame of the cell,
+//   q(xi, eta) = q0 + q1 xi + q2 eta + q3 xi^2 + q4 xi eta + q5 eta^2.
+template <typename R, int m>
+__device__ __forceinline__ void reconstruct_component(const GeoView<R>& G, const R* __restrict__ U, int N, int i,
+                                                      const int src[3], int c, const EqParams& P, R q[6]) {
+  const R W0 = U[(size_t)(0 * m + c) * N + i];
+  const R V0 = U[(size_t)(1 * m + c) * N + i];
+  const R Y0 = U[(size_t)(2 * m + c) * N + i];
+  R Wl[3], Vl[3], Yl[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    Wl[l] = U[(size_t)(0 * m + c) * N + src[l]];
+    Vl[l] = U[(size_t)(1 * m + c) * N + src[l]];
+    Yl[l] = U[(size_t)(2 * m + c) * N + src[l]];
+  }
+  // Step 1: constrained least squares solved once on the host; here the operator
+  R rhs[9];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    rhs[l] = Wl[l] - W0;
+    const R w = G.r(G_W + l, i);
+    rhs[3 + 2 * l] = V0 + w * (Vl[l] - V0);
+    rhs[4 + 2 * l] = Y0 + w * (Yl[l] - Y0);
+  }
+  R cc[5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    R s = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s += G.r(G_M1 + r * 9 + k, i) * rhs[k];
+    cc[r] = s;
+  }
+  // Step 2: linear polynomials on {K0, K_l}
+  R b[3][2];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      b[l][r] = G.r(G_P + l * 6 + r * 3 + 0, i) * (Wl[l] - W0) + G.r(G_P + l * 6 + r * 3 + 1, i) * Vl[l] +
+                G.r(G_P + l * 6 + r * 3 + 2, i) * Yl[l];
+  // Step 4 (Eq. smoo1): in the frame scaled by h0 = sqrt|K0| the factors
+  // |K0|^|s| cancel the chain-rule factors, leaving the scaled derivatives.
+  R beta[4];
+  beta[0] = cc[0] * cc[0] + cc[1] * cc[1] + R(4) * cc[2] * cc[2] + cc[3] * cc[3] + R(4) * cc[4] * cc[4];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) beta[l + 1] = b[l][0] * b[l][0] + b[l][1] * b[l][1];
+  // Step 5
+  const R Wave = (W0 + Wl[0] + Wl[1] + Wl[2]) * R(0.25) + R(1e-30);
+  R om[4];
+  nonlinear_weights(Wave, beta, P.g, P.eps, om);
+  // Step 6: q = (om1/g1) p1 + sum_l (om_l - om1 g_l / g1) p_l
+  const R a1 = om[0] / R(P.g[0]);
+  R al[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) al[l] = om[l + 1] - a1 * R(P.g[l + 1]);
+  R q1 = a1 * cc[0], q2 = a1 * cc[1];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) { q1 += al[l] * b[l][0]; q2 += al[l] * b[l][1]; }
+  const R q3 = a1 * cc[2], q4 = a1 * cc[3], q5 = a1 * cc[4];
+  // the constant parts of p1..p4 all equal Wbar_0 and the coefficients sum to one
+  q[0] = W0 - q3 * G.r(G_MOM, i) - q4 * G.r(G_MOM + 1, i) - q5 * G.r(G_MOM + 2, i);
+  q[1] = q1; q[2] = q2; q[3] = q3; q[4] = q4; q[5] = q5;
+}
+
+// ---------------------------------------------------------------- Lax-Wendroff
+// Second-order jets in (x, y) extended by the time directions t, xt, yt.
+template <typename R> struct Jet {
+  R v, x, y, xx, xy, yy, t, xt, yt;
+};
+template <typename R> __device__ __forceinline__ Jet<R> jadd(const Jet<R>& a, const Jet<R>& b) {
+  return {a.v + b.v, a.x + b.x, a.y + b.y, a.xx + b.xx, a.xy + b.xy, a.yy + b.yy, a.t + b.t, a.xt + b.xt, a.yt + b.yt};
+}
+template <typename R> __device__ __forceinline__ Jet<R> jscale(R s, const Jet<R>& a) {
+  return {s * a.v, s * a.x, s * a.y, s * a.xx, s * a.xy, s * a.yy, s * a.t, s * a.xt, s * a.yt};
+}
+template <typename R> __device__ __forceinline__ Jet<R> jmul(const Jet<R>& a, const Jet<R>& b) {
+  Jet<R> c;
+  c.v = a.v * b.v;
+  c.x = a.x * b.v + a.v * b.x;
+  c.y = a.y * b.v + a.v * b.y;
+  c.xx = a.xx * b.v + R(2) * a.x * b.x + a.v * b.xx;
+  c.xy = a.xy * b.v + a.x * b.y + a.y * b.x + a.v * b.xy;
+  c.yy = a.yy * b.v + R(2) * a.y * b.y + a.v * b.yy;
+  c.t = a.t * b.v + a.v * b.t;
+  c.xt = a.xt * b.v + a.x * b.t + a.t * b.x + a.v * b.xt;
+  c.yt = a.yt * b.v + a.y * b.t + a.t * b.y + a.v * b.yt;
+  return c;
+}
+template <typename R> __device__ __forceinline__ Jet<R> jrecip(const Jet<R>& a) {
+  Jet<R> r;
+  r.v = R(1) / a.v;
+  const R r2 = r.v * r.v;
+  r.x = -a.x * r2;
+  r.y = -a.y * r2;
+  r.t = -a.t * r2;
+  r.xx = -a.xx * r2 - R(2) * a.x * r.v * r.x;
+  r.xy = -a.xy * r2 - R(2) * a.x * r.v * r.y;
+  r.yy = -a.yy * r2 - R(2) * a.y * r.v * r.y;
+  r.xt = -a.xt * r2 - R(2) * a.t * r.v * r.x;
+  r.yt = -a.yt * r2 - R(2) * a.t * r.v * r.y;
+  return r;
+}
+
+// Euler fluxes f, g (Eq. 2d) propagated through jets.
+template <typename R>
+__device__ __forceinline__ void euler_flux_jets(const Jet<R> W[4], R gm1, Jet<R> f[4], Jet<R> g[4]) {
+  const Jet<R> ir = jrecip(W[0]);
+  const Jet<R> u = jmul(W[1], ir), v = jmul(W[2], ir);
+  const Jet<R> mu = jmul(W[1], u), nv = jmul(W[2], v), nu = jmul(W[2], u);
+  const Jet<R> p = jscale(gm1, jadd(W[3], jscale(R(-0.5), jadd(mu, nv))));
+  const Jet<R> H = jadd(W[3], p);
+  f[0] = W[1]; f[1] = jadd(mu, p); f[2] = nu; f[3] = jmul(H, u);
+  g[0] = W[2]; g[1] = nu; g[2] = jadd(nv, p); g[3] = jmul(H, v);
+}
+
+// Lax-Wendroff procedure at one point (Section 2.1): from (W, Wx, Wy) and the
+// cell-constant second derivatives, the first and second time derivatives.
+template <typename R, int EQ>
+__device__ __forceinline__ void lax_wendroff(const R* W, const R* Wx, const R* Wy, const R* Wxx, const R* Wxy,
+                                             const R* Wyy, const EqParams& P, R* Wt, R* Wtt) {
+  if constexpr (EQ == kEqAdvection) {
+    const R ax = R(P.ax), ay = R(P.ay);
+    Wt[0] = -(ax * Wx[0] + ay * Wy[0]);
+    Wtt[0] = ax * ax * Wxx[0] + R(2) * ax * ay * Wxy[0] + ay * ay * Wyy[0];
+  } else if constexpr (EQ == kEqBurgers) {
+    // f = g = W^2 / 2:  Wt = -W s, s = Wx + Wy;  Wtt = -(Wt s + W (Wtx + Wty))
+    const R s = Wx[0] + Wy[0];
+    const R wt = -W[0] * s;
+    const R wtx = -(Wx[0] * s + W[0] * (Wxx[0] + Wxy[0]));
+    const R wty = -(Wy[0] * s + W[0] * (Wxy[0] + Wyy[0]));
+    Wt[0] = wt;
+    Wtt[0] = -(wt * s + W[0] * (wtx + wty));
+  } else {
+    const R gm1 = R(P.gam - 1.0);
+    Jet<R> J[4], f[4], g[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) J[c] = {W[c], Wx[c], Wy[c], Wxx[c], Wxy[c], Wyy[c], R(0), R(0), R(0)};
+    euler_flux_jets(J, gm1, f, g);
+    // Wt = -(f_x + g_y), Wtx = -(f_xx + g_xy), Wty = -(f_xy + g_yy)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      J[c].t = -(f[c].x + g[c].y);
+      J[c].xt = -(f[c].xx + g[c].xy);
+      J[c].yt = -(f[c].xy + g[c].yy);
+    }
+    euler_flux_jets(J, gm1, f, g);
+    // Wtt = -(f_xt + g_yt)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { Wt[c] = J[c].t; Wtt[c] = -(f[c].xt + g[c].yt); }
+  }
+}
+
+// ---------------------------------------------------------------- fluxes
+// F(W) . n
+template <typename R, int EQ>
+__device__ __forceinline__ void flux_n(const R* W, R nx, R ny, const EqParams& P, R* H) {
+  if constexpr (EQ == kEqAdvection) {
+    H[0] = (R(P.ax) * nx + R(P.ay) * ny) * W[0];
+  } else if constexpr (EQ == kEqBurgers) {
+    H[0] = R(0.5) * W[0] * W[0] * (nx + ny);
+  } else {
+    const R ir = R(1) / W[0];
+    const R u = W[1] * ir, v = W[2] * ir;
+    const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
+    const R un = u * nx + v * ny;
+    H[0] = W[0] * un;
+    H[1] = W[1] * un + p * nx;
+    H[2] = W[2] * un + p * ny;
+    H[3] = (W[3] + p) * un;
+  }
+}
+
+// Largest eigenvalue in magnitude of d(F.n)/dW at a cell average.
+template <typename R, int EQ>
+__device__ __forceinline__ R spectral_radius_n(const R* W, R nx, R ny, const EqParams& P) {
+  if constexpr (EQ == kEqAdvection) {
+    return fabs(R(P.ax) * nx + R(P.ay) * ny);
+  } else if constexpr (EQ == kEqBurgers) {
+    return fabs(W[0] * (nx + ny));
+  } else {
+    const R ir = R(1) / W[0];
+    const R u = W[1] * ir, v = W[2] * ir;
+    const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
+    return fabs(u * nx + v * ny) + sqrt(R(P.gam) * p * ir);
+  }
+}
+
+// Spectral radius over all directions (CFL time step).
+template <typename R, int EQ>
+__device__ __forceinline__ double spectral_radius_all(const R* W, const EqParams& P) {
+  if constexpr (EQ == kEqAdvection) {
+    return sqrt(P.ax * P.ax + P.ay * P.ay);
+  } else if constexpr (EQ == kEqBurgers) {
+    return 1.4142135623730951 * fabs((double)W[0]);
+  } else {
+    const double r = W[0], mx = W[1], my = W[2], E = W[3];
+    const double u = mx / r, v = my / r;
+    const double p = (P.gam - 1.0) * (E - 0.5 * (mx * u + my * v));
+    return sqrt(u * u + v * v) + sqrt(P.gam * p / r);
+  }
+}
+
+template <typename R, int EQ> __device__ __forceinline__ bool physical(const R* W, const EqParams& P) {
+  constexpr int m = EqTraits<EQ>::m;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < m; ++c) ok = ok && isfinite(W[c]);
+  if constexpr (EQ == kEqEuler) {
+    if (ok) {
+      const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+      ok = (W[0] > R(0)) && (p > R(0));
+    }
+  }
+  return ok;
+}
+
+}  // namespace hw

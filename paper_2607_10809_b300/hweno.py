@@ -1,0 +1,214 @@
+"""Thin Python binding of the C ABI in include/hweno.h (argument marshalling only).
+
+Every step of the scheme runs in the CUDA library; this module only converts
+numpy arrays to pointers, allocates the device workspace as a torch uint8
+tensor and passes torch's current CUDA stream.  It fails loudly when the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhweno.so")
+
+HW_OK, HW_EINVAL, HW_ENOMEM, HW_ECUDA, HW_EMESH, HW_ENONFINITE, HW_ETIMEOUT, HW_ESTATE = range(8)
+STATUS_NAMES = ["HW_OK", "HW_EINVAL", "HW_ENOMEM", "HW_ECUDA", "HW_EMESH", "HW_ENONFINITE", "HW_ETIMEOUT",
+                "HW_ESTATE"]
+EQUATIONS = {"advection": 0, "burgers": 1, "euler": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+# every symbol declared in include/hweno.h
+EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_ntri", "hw_mesh_neighbors",
+            "hw_mesh_permutation", "hw_workspace_bytes", "hw_state_init", "hw_set_state", "hw_step", "hw_run_to",
+            "hw_get_state", "hw_conservation", "hw_status_flags", "hw_time", "hw_solver_destroy", "hw_last_error"]
+
+
+class HwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eq", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("ax", ctypes.c_double),
+                ("ay", ctypes.c_double), ("gamma_gas", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("gamma_lin", ctypes.c_double * 4), ("eps", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libhweno.so (built by paper_2607_10809_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2607_10809_b300/build.py (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, d, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "hw_options_default": (None, [P(Options)]),
+        "hw_mesh_create": (ctypes.c_int, [vp, i64, vp, i64, d, d, i32, P(vp)]),
+        "hw_mesh_destroy": (ctypes.c_int, [vp]),
+        "hw_mesh_ntri": (i64, [vp]),
+        "hw_mesh_neighbors": (ctypes.c_int, [vp, vp, vp]),
+        "hw_mesh_permutation": (ctypes.c_int, [vp, vp]),
+        "hw_workspace_bytes": (ctypes.c_int, [vp, P(Options), i32, P(sz)]),
+        "hw_state_init": (ctypes.c_int, [vp, P(Options), i32, vp, vp, vp, vp, sz, vp, P(vp)]),
+        "hw_set_state": (ctypes.c_int, [vp, vp, vp, vp, d]),
+        "hw_step": (ctypes.c_int, [vp, d]),
+        "hw_run_to": (ctypes.c_int, [vp, d, P(i64)]),
+        "hw_get_state": (ctypes.c_int, [vp, vp, vp, vp, P(d)]),
+        "hw_conservation": (ctypes.c_int, [vp, vp]),
+        "hw_status_flags": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
+        "hw_time": (ctypes.c_int, [vp, P(d), P(d), P(i64)]),
+        "hw_solver_destroy": (ctypes.c_int, [vp]),
+        "hw_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != HW_OK:
+        raise HwError(rc, load().hw_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def options(eq="advection", a=(1.0, 1.0), gamma_gas=1.4, cfl=0.5, gamma_lin=(0.94, 0.02, 0.02, 0.02), eps=1e-8):
+    o = Options()
+    load().hw_options_default(ctypes.byref(o))
+    o.eq = EQUATIONS[eq]
+    o.ax, o.ay = a
+    o.gamma_gas = gamma_gas
+    o.cfl = cfl
+    for k in range(4):
+        o.gamma_lin[k] = gamma_lin[k]
+    o.eps = eps
+    return o
+
+
+# ------------------------------------------------------------------ C-ABI names
+def hw_mesh_create(xy, tri, Lx=0.0, Ly=0.0, bc=0):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().hw_mesh_create(_ptr(xy), xy.shape[0], _ptr(tri), tri.shape[0], float(Lx), float(Ly), int(bc),
+                                 ctypes.byref(h)))
+    return h
+
+
+def hw_mesh_neighbors(h, nt):
+    nbr = np.empty((nt, 3), np.int32); nbe = np.empty((nt, 3), np.int32)
+    _check(load().hw_mesh_neighbors(h, _ptr(nbr), _ptr(nbe)))
+    return nbr, nbe
+
+
+def hw_mesh_permutation(h, nt):
+    p = np.empty(nt, np.int32)
+    _check(load().hw_mesh_permutation(h, _ptr(p)))
+    return p
+
+
+def hw_workspace_bytes(h, opt, precision):
+    n = ctypes.c_size_t()
+    _check(load().hw_workspace_bytes(h, ctypes.byref(opt), PRECISIONS[precision], ctypes.byref(n)))
+    return n.value
+
+
+class Mesh:
+    """Host mesh handle (hw_mesh)."""
+
+    def __init__(self, mesh):
+        self.src = mesh
+        self.nt = mesh.nt
+        self.h = hw_mesh_create(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, mesh.bc)
+
+    def neighbors(self):
+        return hw_mesh_neighbors(self.h, self.nt)
+
+    def permutation(self):
+        return hw_mesh_permutation(self.h, self.nt)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.hw_mesh_destroy(self.h)
+            self.h = None
+
+
+class Solver:
+    """One solve on the current CUDA device (hw_solver).  State arrays follow
+    the host layout U[k, c, i] (k: Wbar, Vbar, Ybar) in the caller's numbering."""
+
+    def __init__(self, mesh, U0, eq="advection", precision="fp64", stream=None, **opt_kw):
+        import torch
+        self.mesh = mesh if isinstance(mesh, Mesh) else Mesh(mesh)
+        self.m = 4 if eq == "euler" else 1
+        self.eq = eq
+        self.precision = precision
+        self.opt = options(eq, **opt_kw)
+        nbytes = hw_workspace_bytes(self.mesh.h, self.opt, precision)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        U0 = np.ascontiguousarray(U0, dtype=np.float64)
+        assert U0.shape == (3, self.m, self.mesh.nt), U0.shape
+        h = ctypes.c_void_p()
+        _check(load().hw_state_init(self.mesh.h, ctypes.byref(self.opt), PRECISIONS[precision], _ptr(U0[0]),
+                                    _ptr(U0[1]), _ptr(U0[2]), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def set_state(self, U, t=0.0):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        _check(load().hw_set_state(self.h, _ptr(U[0]), _ptr(U[1]), _ptr(U[2]), float(t)))
+        self._keep = U   # the copy is asynchronous
+
+    def step(self, dt=0.0):
+        _check(load().hw_step(self.h, float(dt)))
+
+    def run_to(self, T):
+        n = ctypes.c_int64()
+        _check(load().hw_run_to(self.h, float(T), ctypes.byref(n)))
+        return n.value
+
+    def get_state(self):
+        U = np.empty((3, self.m, self.mesh.nt))
+        t = ctypes.c_double()
+        _check(load().hw_get_state(self.h, _ptr(U[0]), _ptr(U[1]), _ptr(U[2]), ctypes.byref(t)))
+        return U, t.value
+
+    def conservation(self):
+        s = np.empty(self.m)
+        _check(load().hw_conservation(self.h, _ptr(s)))
+        return s
+
+    def status_flags(self):
+        f = ctypes.c_uint32()
+        _check(load().hw_status_flags(self.h, ctypes.byref(f)))
+        return f.value
+
+    def time(self):
+        t = ctypes.c_double(); dt = ctypes.c_double(); n = ctypes.c_int64()
+        _check(load().hw_time(self.h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(n)))
+        return t.value, dt.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.hw_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,103 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+declared symbol, and its FP64 mesh precompute matches the oracle bit for bit
+on connectivity."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_10809_b300 import build as B
+from paper_2607_10809_b300 import hweno
+from paper_2607_10809_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return hweno.load()
+
+
+def header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(hw_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(hweno.EXPORTED)
+
+
+MESHES = {
+    "structured": lambda: I.config1_mesh(10),
+    "jittered": lambda: I.jittered_periodic(9, 4.0, seed=2),
+    "poisson": lambda: I.poisson_delaunay_periodic(10.0, 400, seed=3),
+    "box": lambda: I.jittered_box(8, seed=4),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_connectivity_bit_exact_against_oracle(lib, name):
+    mesh = MESHES[name]()
+    m = hweno.Mesh(mesh)
+    nbr, nbe = m.neighbors()
+    onbr, onbe = oracle.Oracle(mesh).neighbors()
+    np.testing.assert_array_equal(nbr, onbr)
+    np.testing.assert_array_equal(nbe, onbe)
+
+
+def test_hilbert_order_is_a_permutation_with_local_neighbours(lib):
+    mesh = I.jittered_periodic(64, 4.0, seed=2)
+    m = hweno.Mesh(mesh)
+    p = m.permutation()
+    assert np.array_equal(np.sort(p), np.arange(mesh.nt))
+    inv = np.empty_like(p); inv[p] = np.arange(mesh.nt)
+    nbr, _ = m.neighbors()
+    d = np.abs(inv[nbr] - inv[:, None])
+    # most neighbours lie within a few warps of each other in the internal order
+    assert np.median(d) < 64
+    assert np.mean(d < 1024) > 0.9
+
+
+def test_mesh_errors_are_reported(lib):
+    mesh = I.jittered_periodic(4, 1.0, seed=1)
+    bad = mesh.tri.copy(); bad[0, 0] = mesh.nv + 5
+    with pytest.raises(hweno.HwError) as e:
+        hweno.hw_mesh_create(mesh.xy, bad, 1.0, 1.0, 0)
+    assert e.value.status == hweno.HW_EINVAL
+    dup = np.concatenate([mesh.tri, mesh.tri[:1]])
+    with pytest.raises(hweno.HwError) as e:
+        hweno.hw_mesh_create(mesh.xy, dup, 1.0, 1.0, 0)
+    assert e.value.status == hweno.HW_EMESH
+    cw = mesh.tri.copy(); cw[3] = cw[3, ::-1]
+    with pytest.raises(hweno.HwError) as e:
+        hweno.hw_mesh_create(mesh.xy, cw, 1.0, 1.0, 0)
+    assert e.value.status == hweno.HW_EMESH
+    box = I.jittered_box(4)
+    with pytest.raises(hweno.HwError) as e:   # open boundary declared periodic
+        hweno.hw_mesh_create(box.xy, box.tri, 1.0, 1.0, 0)
+    assert e.value.status == hweno.HW_EMESH
+    assert "open edge" in str(e.value)
+
+
+def test_workspace_grows_with_mesh_and_precision(lib):
+    a = hweno.Mesh(I.jittered_periodic(8, 1.0, seed=1))
+    b = hweno.Mesh(I.jittered_periodic(16, 1.0, seed=1))
+    o = hweno.options("euler")
+    wa64 = hweno.hw_workspace_bytes(a.h, o, "fp64")
+    wb64 = hweno.hw_workspace_bytes(b.h, o, "fp64")
+    wb32 = hweno.hw_workspace_bytes(b.h, o, "fp32")
+    assert wb64 > 3.5 * wa64 and wb32 < wb64
+    with pytest.raises(hweno.HwError):
+        hweno.hw_workspace_bytes(a.h, hweno.options("euler", cfl=-1.0), "fp64")
