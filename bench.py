@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of one ADER-HWENO time step on a B300: triangle-updates per second.
+
+Workload (default): 2D Euler isentropic vortex (strength 5, background
+(1, 1, 1, 1), gamma 1.4) on the periodic square [0, 10]^2, meshed by a
+periodic Delaunay triangulation of a seeded Poisson-disk point set (about
+1.0M points, 2.0M triangles).  Synthetic inputs, built on the host.
+
+A step is one full pass of the scheme over every triangle and edge:
+reconstruction + Lax-Wendroff (k_recon), then flux, cell-average and
+Green-Gauss update and the next CFL step (k_edge).  The headline line is the
+FP32 form; the FP64 form is measured on the same mesh and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method does not shard across GPUs here); value = all ranks' triangle
+updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_10809_b300 import inputs as I  # noqa: E402
+
+METRIC = "triangle-updates/s (Euler, 2M tris)"
+UNIT = "tri-updates/s"
+
+# Algorithmic bytes per cell and step of each kernel, per precision word s
+# (4 or 8 bytes), for the Euler system (m = 4):
+#   k_recon reads the cell state 3m words, the reconstruction geometry 76 words
+#   and 3 neighbour indices; writes the edge-point buffer 6 * 3 * m words.
+#   k_edge reads the edge-point buffer 6 * 3 * m words, the cell averages m
+#   words, 10 geometry words and 4 index words; writes the state 3m words.
+# Neighbour data are counted once (perfect reuse through the caches).
+def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
+    if kernel == "recon":
+        return (3 * m + 76 + 18 * m) * s + 3 * 4
+    return (18 * m + m + 10 + 3 * m) * s + 4 * 4
+
+
+# DRAM traffic per cell (bytes) measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
+# it was measured on; it is reported only while the sources are unchanged.
+TRAFFIC = {
+    "sources_sha": "885570ae281969f5",
+    "per_cell": {"recon_fp32": 571.2, "edge_fp32": 403.6},   # 499,942-cell capture, scaled per cell
+}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "device.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2607_10809_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.dev), "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.25)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- workload
+def workload(name: str):
+    if name == "vortex2m":
+        mesh = I.config3_mesh(1_000_000, seed=3)
+    elif name == "vortex500k":
+        mesh = I.config3_mesh(250_000, seed=3)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    U0 = I.initial_state(mesh, I.vortex, 4)
+    return mesh, U0
+
+
+def sample_patch(geo, n):
+    """About n cells nearest to the vortex centre: a contiguous patch."""
+    d = (geo["cx"] - 5.0) ** 2 + (geo["cy"] - 5.0) ** 2
+    return np.argsort(d, kind="stable")[:n]
+
+
+def cpu_oracle_rate(mesh, U0, target_seconds=12.0):
+    """The FP64 oracle, single-threaded, one masked step over a patch of cells;
+    the patch grows until the step takes about target_seconds."""
+    import oracle
+    o = oracle.Oracle(mesh, "euler")
+    geo = o.cell_geometry()
+    dt = 0.5 * o.cfl_dt(U0)
+    n = 2000
+    while True:
+        mask = np.zeros(mesh.nt, np.uint8)
+        mask[sample_patch(geo, n)] = 1
+        t0 = time.perf_counter()
+        o.step(U0, dt, mask=mask)
+        el = time.perf_counter() - t0
+        if el > target_seconds / 4 or n * 2 > mesh.nt:
+            break
+        n *= 2
+    return n / el, n, el
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2607_10809_b300 import build as B
+    from paper_2607_10809_b300 import hweno
+
+    torch.cuda.set_device(local_rank)
+    B.build()
+    hweno.load()
+    mesh, U0 = workload(args.workload)
+    N = mesh.nt
+    hmesh = hweno.Mesh(mesh)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    precs = ("fp32", "fp64") if args.only == "both" else (args.only,)
+    for prec in precs:
+        K = args.steps if prec == "fp32" else max(3, args.steps // args.fp64_divisor)
+        s = hweno.Solver(hmesh, U0, eq="euler", precision=prec)
+        stream = s.stream
+        for _ in range(args.warmup):
+            s.step()
+        torch.cuda.synchronize(); barrier(); torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        s.profile(True)
+        with ClockSampler(local_rank) as clk:
+            e0.record(stream)
+            for _ in range(K):
+                s.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier(); torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        prof = s.profile_read()
+        s.profile(False)
+        flags = s.status_flags()
+        results[prec] = {"K": K, "ms": ms, "prof": prof, "clocks": clk.summary(), "flags": flags}
+        if prec == "fp32" and not args.no_e2e:
+            # end to end through the C ABI with host buffers: H2D state, step, D2H state
+            Upin = torch.empty((3, 4, N), dtype=torch.float64, pin_memory=True).numpy()
+            Upin[...] = U0
+            Uout = torch.empty((3, 4, N), dtype=torch.float64, pin_memory=True).numpy()
+            Ke = max(3, min(K, args.e2e_steps))
+            s.set_state(Upin); s.step(); s.get_state(out=Uout)
+            torch.cuda.synchronize(); barrier()
+            t0 = time.perf_counter()
+            for _ in range(Ke):
+                s.set_state(Upin)
+                s.step()
+                s.get_state(out=Uout)
+            el = max_over_ranks(time.perf_counter() - t0)
+            results["e2e"] = {"steps": Ke, "s": el, "bytes": 3 * 4 * N * 8}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    if args.only != "both" or args.no_e2e:
+        print(json.dumps({"partial_run": True, "N": N, **{k: v for k, v in results.items()}}), flush=True)
+        return
+    hbm, peak_kind = measured_peaks()
+    r32 = results["fp32"]
+    K = r32["K"]
+    value = world * N * K / (r32["ms"] * 1e-3)
+    rec_ms = r32["prof"]["recon_ms"] / max(1, r32["prof"]["steps"])
+    edge_ms = r32["prof"]["edge_ms"] / max(1, r32["prof"]["steps"])
+    dom = "recon" if rec_ms >= edge_ms else "edge"
+    dom_ms = max(rec_ms, edge_ms)
+    achieved = alg_bytes(dom, 4) * N / (dom_ms * 1e-3) / 1e9
+    sha = kernel_sources_sha()
+    tr = TRAFFIC["per_cell"].get(f"{dom}_fp32") if TRAFFIC["sources_sha"] == sha else None
+    r64 = results["fp64"]
+    rec64 = r64["prof"]["recon_ms"] / max(1, r64["prof"]["steps"])
+    edge64 = r64["prof"]["edge_ms"] / max(1, r64["prof"]["steps"])
+    e2e = results["e2e"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": r32["ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"euler-isentropic-vortex, periodic [0,10]^2, Poisson-disk Delaunay, {N} triangles",
+                   "triangles": N, "equation": "euler", "precision": "fp32 state/arithmetic, fp64 precompute",
+                   "l2": "inputs larger than L2 (working set %.2f GB)" % (
+                       (86 * 4 + 16 + 2 * 48 + 288) * N / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single-gpu"},
+        "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "alg_bytes_per_cell": alg_bytes(dom, 4),
+                     "traffic": (tr * N) if tr else None,
+                     "kernel_ms": {"k_recon": rec_ms, "k_edge": edge_ms}},
+        "e2e": {"value": world * N * e2e["steps"] / e2e["s"], "unit": UNIT,
+                "h2d_bytes_per_step": e2e["bytes"], "d2h_bytes_per_step": e2e["bytes"]},
+        "gpu_launches": 2 * K,
+        "clocks": r32["clocks"],
+        "fp64": {"value": world * N * r64["K"] / (r64["ms"] * 1e-3), "steps": r64["K"],
+                 "ms_per_step": r64["ms"] / r64["K"], "kernel_ms": {"k_recon": rec64, "k_edge": edge64},
+                 "clocks": r64["clocks"]},
+        "status_flags": {"fp32": r32["flags"], "fp64": r64["flags"]},
+    }
+    if not args.no_cpu:
+        import multiprocessing as mp  # noqa: F401  (oracle runs in this process, single thread)
+        rate, n, el = cpu_oracle_rate(mesh, U0, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 oracle step over a patch of {n} of {N} cells ({el:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as the reference arm: each step is one oracle step
+    over a fixed patch of cells of the same workload, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    mesh, U0 = workload(args.workload)
+    o = oracle.Oracle(mesh, "euler")
+    geo = o.cell_geometry()
+    n = args.ref_cells
+    mask = np.zeros(mesh.nt, np.uint8)
+    mask[sample_patch(geo, n)] = 1
+    dt = 0.5 * o.cfl_dt(U0)
+    for _ in range(args.warmup):
+        o.step(U0, dt, mask=mask)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(U0, dt, mask=mask)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"euler-isentropic-vortex, periodic [0,10]^2, Poisson-disk Delaunay, {mesh.nt} triangles",
+                       "triangles": mesh.nt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle step over a patch of {n} of {mesh.nt} cells"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="vortex2m", choices=["vortex2m", "vortex500k"])
+    ap.add_argument("--fp64-divisor", type=int, default=20, help="FP64 timed steps = steps / divisor")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64"], help="precisions to run")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-cells", type=int, default=4000)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

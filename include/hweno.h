@@ -132,6 +132,14 @@ hw_status hw_conservation(hw_solver* s, double* sums);
 hw_status hw_status_flags(hw_solver* s, uint32_t* flags);
 /* Current time, current device time step and steps taken; synchronises. */
 hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps);
+/* Per-kernel timing of the next hw_step calls (up to 4096 steps) with CUDA
+ * events on the solver's stream, for measurement; enable = 0 stops it.
+ * Enabling resets the accumulators. */
+hw_status hw_profile(hw_solver* s, int32_t enable);
+/* Synchronises on the recorded events; ms[0] = total reconstruction-kernel
+ * time, ms[1] = total flux/update-kernel time (milliseconds) over nsteps
+ * profiled steps. */
+hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps);
 hw_status hw_solver_destroy(hw_solver* s);
 
 /* Message of the last failing call on this thread. */

@@ -586,17 +586,15 @@ const double kGL = 0.28867513459481288225;  // sqrt(3)/6
 const double kTau[3] = {0.0, 0.5, 1.0};                  // R2: Lobatto nodes
 const double kWt[3] = {1.0 / 6.0, 4.0 / 6.0, 1.0 / 6.0};  // R2: Lobatto weights
 
-// Taylor data (W, Wt, Wtt) at the two Gauss points of edge e, for side L
-// (evaluated in L's frame) and for side R (neighbour's own reconstruction, its
-// frame).  Returns the Taylor data per Gauss point g, indexed along the edge
-// from A to B as seen by L.
+// Taylor data (W, Wt, Wtt) at the point (x, y) of a cell's own frame from the
+// cell's reconstructions rec[0..m-1] (Eq. recon, then Section 2.1).
 template <class S>
-void side_taylor(const Problem& pb, const CellRecon<S>* rec, int64_t cell, double x, double y, S W[4], S Wt[4], S Wtt[4]) {
+void side_taylor(const Problem& pb, const CellRecon<S>* rec, double x, double y, S W[4], S Wt[4], S Wtt[4]) {
   const int m = pb.P.m;
   S J[6][4];
   for (int c = 0; c < m; ++c) {
     S o[6];
-    recon_at(rec[cell * m + c], pb.P.glin, x, y, o);
+    recon_at(rec[c], pb.P.glin, x, y, o);
     for (int d = 0; d < 6; ++d) J[d][c] = o[d];
   }
   S Wtx[4], Wty[4];
@@ -619,12 +617,16 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
         for (int j = 0; j < 3; ++j) if (pb.nbr[i][j] >= 0) need[pb.nbr[i][j]] = 1;
       }
   }
-  std::vector<CellRecon<S>> rec(nt * m);
+  // reconstructions of the needed cells, stored compactly (slot[i] -> position)
+  std::vector<int64_t> slot(nt, -1);
+  int64_t nneed = 0;
+  for (int64_t i = 0; i < nt; ++i) if (need[i]) slot[i] = nneed++;
+  std::vector<CellRecon<S>> rec(nneed * m);
   for (int64_t i = 0; i < nt; ++i) {
     if (!need[i]) continue;
     for (int c = 0; c < m; ++c) {
-      rec[i * m + c] = reconstruct(pb, U, i, c);
-      if (!rec[i * m + c].ok) { g_err = "singular reconstruction system"; return 4; }
+      rec[slot[i] * m + c] = reconstruct(pb, U, i, c);
+      if (!rec[slot[i] * m + c].ok) { g_err = "singular reconstruction system"; return 4; }
     }
   }
   std::vector<S> Rf(nt * m, S(0.0)), GV(nt * m, S(0.0)), GY(nt * m, S(0.0));
@@ -645,9 +647,9 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
       double s = (gi == 0) ? 0.5 - kGL : 0.5 + kGL;
       double x = e.Ax + s * (e.Bx - e.Ax), y = e.Ay + s * (e.By - e.Ay);
       S Wi[4], Wti[4], Wtti[4], We[4], Wte[4], Wtte[4];
-      side_taylor(pb, rec.data(), e.L, x, y, Wi, Wti, Wtti);
+      side_taylor(pb, rec.data() + slot[e.L] * m, x, y, Wi, Wti, Wtti);
       if (e.R >= 0) {
-        side_taylor(pb, rec.data(), e.R, x - e.sx, y - e.sy, We, Wte, Wtte);
+        side_taylor(pb, rec.data() + slot[e.R] * m, x - e.sx, y - e.sy, We, Wte, Wtte);
       } else {
         for (int c = 0; c < m; ++c) { We[c] = Wi[c]; Wte[c] = Wti[c]; Wtte[c] = Wtti[c]; }
       }

@@ -84,6 +84,10 @@ struct hw_solver {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   DevScalars* h_sc = nullptr;  // pinned mirror for readback
   double* h_consv = nullptr;
+  // per-kernel event timing (hw_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;  // 3 per profiled step: before recon, between, after edge
+  int64_t nprof = 0;
 
   void* U(int k) { return ws + (k == 0 ? L.U0 : L.U1); }
   DevScalars* sc() { return reinterpret_cast<DevScalars*>(ws + L.sc); }
@@ -231,9 +235,22 @@ hw_status hw_set_state(hw_solver* s, const double* Wbar, const double* Vbar, con
   return upload_state(s, Wbar, Vbar, Ybar, t);
 }
 
+constexpr int64_t kMaxProfiledSteps = 4096;
+
 hw_status hw_step(hw_solver* s, double dt) {
   if (!s) return fail(HW_EINVAL, "null solver");
-  launch_step(s->prec, s->eq, s->args(s->cur, dt > 0 ? dt : 0.0), s->stream);
+  const StepArgs a = s->args(s->cur, dt > 0 ? dt : 0.0);
+  if (s->profiling && s->nprof < kMaxProfiledSteps) {
+    cudaEvent_t* e = &s->ev[3 * s->nprof];
+    HW_CUDA(cudaEventRecord(e[0], s->stream));
+    launch_recon(s->prec, s->eq, a, s->stream);
+    HW_CUDA(cudaEventRecord(e[1], s->stream));
+    launch_edge(s->prec, s->eq, a, s->stream);
+    HW_CUDA(cudaEventRecord(e[2], s->stream));
+    ++s->nprof;
+  } else {
+    launch_step(s->prec, s->eq, a, s->stream);
+  }
   HW_CUDA(cudaGetLastError());
   s->cur = 1 - s->cur;
   return HW_OK;
@@ -329,8 +346,35 @@ hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps) {
   return HW_OK;
 }
 
+hw_status hw_profile(hw_solver* s, int32_t enable) {
+  if (!s) return fail(HW_EINVAL, "null solver");
+  if (enable && s->ev.empty()) {
+    s->ev.resize(3 * kMaxProfiledSteps);
+    for (auto& e : s->ev) HW_CUDA(cudaEventCreate(&e));
+  }
+  s->profiling = enable != 0;
+  s->nprof = 0;
+  return HW_OK;
+}
+
+hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps) {
+  if (!s || !ms) return fail(HW_EINVAL, "null pointer");
+  ms[0] = ms[1] = 0.0;
+  for (int64_t k = 0; k < s->nprof; ++k) {
+    float a = 0.f, b = 0.f;
+    HW_CUDA(cudaEventSynchronize(s->ev[3 * k + 2]));
+    HW_CUDA(cudaEventElapsedTime(&a, s->ev[3 * k], s->ev[3 * k + 1]));
+    HW_CUDA(cudaEventElapsedTime(&b, s->ev[3 * k + 1], s->ev[3 * k + 2]));
+    ms[0] += a;
+    ms[1] += b;
+  }
+  if (nsteps) *nsteps = s->nprof;
+  return HW_OK;
+}
+
 hw_status hw_solver_destroy(hw_solver* s) {
   if (!s) return HW_OK;
+  for (auto& e : s->ev) cudaEventDestroy(e);
   for (int p = 0; p < 2; ++p)
     if (s->graph[p]) cudaGraphExecDestroy(s->graph[p]);
   if (s->cap_stream) cudaStreamDestroy(s->cap_stream);

@@ -319,12 +319,15 @@ __global__ void k_set_target(DevScalars* sc, double T, int has_T) {
 
 // ---------------------------------------------------------------- launchers
 namespace {
-template <typename R, int EQ> void launch_step_t(const StepArgs& a, cudaStream_t st) {
+template <typename R, int EQ> void launch_recon_t(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N};
-  const int nb = (a.N + 127) / 128;
-  k_recon<R, EQ><<<nb, 128, 0, st>>>(G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb), a.P, a.sc);
-  k_edge<R, EQ><<<nb, 128, 0, st>>>(G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
-                                     reinterpret_cast<const R*>(a.Pb), a.P, a.sc, a.dt_fixed);
+  k_recon<R, EQ><<<(a.N + 127) / 128, 128, 0, st>>>(G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb),
+                                                     a.P, a.sc);
+}
+template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N};
+  k_edge<R, EQ><<<(a.N + 127) / 128, 128, 0, st>>>(G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
+                                                    reinterpret_cast<const R*>(a.Pb), a.P, a.sc, a.dt_fixed);
 }
 template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N};
@@ -332,29 +335,27 @@ template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t 
 }
 }  // namespace
 
+#define HW_DISPATCH(fn, prec, eq, ...)                 \
+  do {                                                 \
+    if ((prec) == 0) {                                 \
+      if ((eq) == 0) fn<double, 0>(__VA_ARGS__);       \
+      else if ((eq) == 1) fn<double, 1>(__VA_ARGS__);  \
+      else fn<double, 2>(__VA_ARGS__);                 \
+    } else {                                           \
+      if ((eq) == 0) fn<float, 0>(__VA_ARGS__);        \
+      else if ((eq) == 1) fn<float, 1>(__VA_ARGS__);   \
+      else fn<float, 2>(__VA_ARGS__);                  \
+    }                                                  \
+  } while (0)
+
+void launch_recon(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_recon_t, prec, eq, a, st); }
+void launch_edge(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_edge_t, prec, eq, a, st); }
 void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st) {
-  if (prec == 0) {
-    if (eq == 0) launch_step_t<double, 0>(a, st);
-    else if (eq == 1) launch_step_t<double, 1>(a, st);
-    else launch_step_t<double, 2>(a, st);
-  } else {
-    if (eq == 0) launch_step_t<float, 0>(a, st);
-    else if (eq == 1) launch_step_t<float, 1>(a, st);
-    else launch_step_t<float, 2>(a, st);
-  }
+  launch_recon(prec, eq, a, st);
+  launch_edge(prec, eq, a, st);
 }
 
-void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st) {
-  if (prec == 0) {
-    if (eq == 0) launch_cfl_t<double, 0>(a, st);
-    else if (eq == 1) launch_cfl_t<double, 1>(a, st);
-    else launch_cfl_t<double, 2>(a, st);
-  } else {
-    if (eq == 0) launch_cfl_t<float, 0>(a, st);
-    else if (eq == 1) launch_cfl_t<float, 1>(a, st);
-    else launch_cfl_t<float, 2>(a, st);
-  }
-}
+void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_cfl_t, prec, eq, a, st); }
 
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st) { k_reset<<<1, 32, 0, st>>>(sc, t, cfl); }
 

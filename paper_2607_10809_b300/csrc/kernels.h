@@ -22,6 +22,8 @@ struct StepArgs {
   EqParams P;
 };
 
+void launch_recon(int prec, int eq, const StepArgs& a, cudaStream_t st);
+void launch_edge(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st);

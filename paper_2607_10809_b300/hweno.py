@@ -24,7 +24,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1}
 # every symbol declared in include/hweno.h
 EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_ntri", "hw_mesh_neighbors",
             "hw_mesh_permutation", "hw_workspace_bytes", "hw_state_init", "hw_set_state", "hw_step", "hw_run_to",
-            "hw_get_state", "hw_conservation", "hw_status_flags", "hw_time", "hw_solver_destroy", "hw_last_error"]
+            "hw_get_state", "hw_conservation", "hw_status_flags", "hw_time", "hw_profile", "hw_profile_read",
+            "hw_solver_destroy", "hw_last_error"]
 
 
 class HwError(RuntimeError):
@@ -68,6 +69,8 @@ def load():
         "hw_conservation": (ctypes.c_int, [vp, vp]),
         "hw_status_flags": (ctypes.c_int, [vp, P(ctypes.c_uint32)]),
         "hw_time": (ctypes.c_int, [vp, P(d), P(d), P(i64)]),
+        "hw_profile": (ctypes.c_int, [vp, i32]),
+        "hw_profile_read": (ctypes.c_int, [vp, vp, P(i64)]),
         "hw_solver_destroy": (ctypes.c_int, [vp]),
         "hw_last_error": (ctypes.c_char_p, []),
     }
@@ -184,8 +187,11 @@ class Solver:
         _check(load().hw_run_to(self.h, float(T), ctypes.byref(n)))
         return n.value
 
-    def get_state(self):
-        U = np.empty((3, self.m, self.mesh.nt))
+    def get_state(self, out=None):
+        """Returns (U, t); ``out`` may be a preallocated float64 array [3, m, nt]
+        (pinned memory makes the device-to-host copy direct)."""
+        U = np.empty((3, self.m, self.mesh.nt)) if out is None else out
+        assert U.shape == (3, self.m, self.mesh.nt) and U.dtype == np.float64 and U.flags.c_contiguous
         t = ctypes.c_double()
         _check(load().hw_get_state(self.h, _ptr(U[0]), _ptr(U[1]), _ptr(U[2]), ctypes.byref(t)))
         return U, t.value
@@ -204,6 +210,14 @@ class Solver:
         t = ctypes.c_double(); dt = ctypes.c_double(); n = ctypes.c_int64()
         _check(load().hw_time(self.h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(n)))
         return t.value, dt.value, n.value
+
+    def profile(self, enable=True):
+        _check(load().hw_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        ms = np.zeros(2); n = ctypes.c_int64()
+        _check(load().hw_profile_read(self.h, _ptr(ms), ctypes.byref(n)))
+        return {"recon_ms": float(ms[0]), "edge_ms": float(ms[1]), "steps": n.value}
 
     def close(self):
         if getattr(self, "h", None) is not None and _lib is not None:

@@ -98,27 +98,28 @@ def jittered_box(n: int, L: float = 1.0, jitter: float = 0.15, seed: int = 0) ->
     return Mesh(xy=xy, tri=tri, Lx=0.0, Ly=0.0, bc=1)
 
 
-def poisson_disk_points(L: float, r: float, seed: int, rounds: int = 24) -> np.ndarray:
+def poisson_disk_points(L: float, r: float, seed: int, attempts: int = 8) -> np.ndarray:
     """Periodic Poisson-disk sample of [0, L)^2 with minimum distance r.
 
     Parallel dart throwing on a background grid of cell size <= r/sqrt(2)
     (each cell holds at most one point); cells are visited in 3x3 phases so
     that cells of one phase are at least 2 cells apart and their candidates
-    cannot conflict with each other."""
+    cannot conflict with each other.  A cell is given up after ``attempts``
+    rejected candidates (the analogue of Bridson's k)."""
     rng = np.random.default_rng(seed)
     G = 3 * int(math.ceil(L / (r / math.sqrt(2.0)) / 3.0))
     cell = L / G
     grid = -np.ones((G, G), dtype=np.int64)
+    fails = np.zeros((G, G), dtype=np.int16)
     px = np.zeros(G * G); py = np.zeros(G * G)
     npts = 0
     offs = [(di, dj) for di in range(-2, 3) for dj in range(-2, 3) if (di, dj) != (0, 0)]
     r2 = r * r
-    for _ in range(rounds):
-        added = 0
+    for _ in range(attempts + 1):
         for pi in range(3):
             for pj in range(3):
-                sub = grid[pi::3, pj::3]
-                I, J = np.nonzero(sub < 0)
+                sub = (grid[pi::3, pj::3] < 0) & (fails[pi::3, pj::3] < attempts)
+                I, J = np.nonzero(sub)
                 if I.size == 0:
                     continue
                 I = I * 3 + pi; J = J * 3 + pj
@@ -127,23 +128,20 @@ def poisson_disk_points(L: float, r: float, seed: int, rounds: int = 24) -> np.n
                 ok = np.ones(I.size, dtype=bool)
                 for di, dj in offs:
                     q = grid[(I + di) % G, (J + dj) % G]
-                    has = q >= 0
-                    if not has.any():
+                    has = np.nonzero((q >= 0) & ok)[0]
+                    if has.size == 0:
                         continue
                     qq = q[has]
                     dx = cx[has] - px[qq]; dy = cy[has] - py[qq]
                     dx -= L * np.floor(dx / L + 0.5); dy -= L * np.floor(dy / L + 0.5)
-                    bad = dx * dx + dy * dy < r2
-                    idx = np.nonzero(has)[0][bad]
-                    ok[idx] = False
+                    ok[has[dx * dx + dy * dy < r2]] = False
                 k = np.nonzero(ok)[0]
                 ids = npts + np.arange(k.size)
                 px[ids] = cx[k]; py[ids] = cy[k]
                 grid[I[k], J[k]] = ids
                 npts += k.size
-                added += k.size
-        if added == 0:
-            break
+                bad = np.nonzero(~ok)[0]
+                fails[I[bad], J[bad]] += 1
     return np.stack([px[:npts], py[:npts]], axis=1)
 
 
@@ -181,8 +179,8 @@ def periodic_delaunay(pts: np.ndarray, L: float, margin: float) -> Mesh:
 def poisson_delaunay_periodic(L: float, target_points: int, seed: int) -> Mesh:
     """Periodic Delaunay mesh of a seeded Poisson-disk point set of about
     ``target_points`` points (about twice as many triangles)."""
-    # dart throwing fills about 0.69 / r^2 points per unit area
-    r = math.sqrt(0.69 * L * L / target_points)
+    # the dart throwing above fills about 0.628 / r^2 points per unit area
+    r = math.sqrt(0.628 * L * L / target_points)
     pts = poisson_disk_points(L, r, seed)
     return periodic_delaunay(pts, L, margin=8.0 * r)
 
