@@ -142,6 +142,26 @@ hw_status hw_profile(hw_solver* s, int32_t enable);
 hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps);
 hw_status hw_solver_destroy(hw_solver* s);
 
+/* Same as hw_step, but the scratch of the step (the edge-point buffer between
+ * the reconstruction and the flux kernels) is a static device array inside the
+ * library instead of part of the workspace.  The paper has no counterpart: it
+ * is for callers that cannot call cudaMalloc (hosts that own the device memory
+ * pool, plug-ins handed fixed buffers, runtimes that must not allocate while
+ * running); they still pass the state and geometry through the solver's
+ * workspace, but need no memory for temporaries.
+ *   - Limit: 18 * m * ntri * (8 for FP64, 4 for FP32) bytes must fit in the
+ *     64 MiB array (FP32 Euler: 233,016 triangles; FP64 Euler: 116,508);
+ *     larger meshes get HW_EINVAL with a message naming both sizes.
+ *   - The array is reserved on every GPU that loads the library, until exit.
+ *   - The first call on a device looks up the array's device address with that
+ *     device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (every slot a step reads is written earlier in the same step, so nothing
+ *     needs clearing); calls whose work overlaps on the GPU (other streams,
+ *     other solvers) race on it and must be serialised by the caller.
+ *   - Allocates nothing (no cudaMalloc, cudaFree or allocating library call). */
+hw_status hw_step_static_scratch(hw_solver* s, double dt);
+
 /* Message of the last failing call on this thread. */
 const char* hw_last_error(void);
 

@@ -5,6 +5,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -385,3 +386,61 @@ hw_status hw_solver_destroy(hw_solver* s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Step without any device allocation by the caller for scratch.
+//
+// Some callers cannot call cudaMalloc at all: code running inside a host that
+// owns the device memory pool and forbids other allocators, plug-ins that are
+// handed fixed buffers, or runtimes that must not allocate once they are
+// running.  For them the edge-point buffer (the only scratch of a step: the
+// Taylor data written by the reconstruction kernel and read back by the flux
+// kernel) lives in the file-scope device array below instead of in the
+// workspace.  Every GPU that loads this library holds the array until the
+// process exits.
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxScratchDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxScratchDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once per
+// device.  In host code the array's name is only a host-side handle, so the
+// kernels must be given this address.
+hw_status static_scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(HW_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxScratchDevices) return fail(HW_EINVAL, "device ordinal out of range for the static scratch");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HW_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return HW_OK;
+}
+}  // namespace
+
+extern "C" hw_status hw_step_static_scratch(hw_solver* s, double dt) {
+  if (!s) return fail(HW_EINVAL, "null solver");
+  const size_t need = (size_t)18 * s->m * s->N * (s->prec == HW_FP64 ? 8 : 4);
+  if (need > kStaticScratchBytes)
+    return fail(HW_EINVAL, "hw_step_static_scratch: the mesh needs " + std::to_string(need) +
+                               " bytes of scratch, more than the static maximum of " +
+                               std::to_string(kStaticScratchBytes) + " bytes; use hw_step");
+  void* scratch = nullptr;
+  if (hw_status st = static_scratch_address(&scratch)) return st;
+  StepArgs a = s->args(s->cur, dt > 0 ? dt : 0.0);
+  a.Pb = scratch;  // every cell's slots are written by k_recon before k_edge reads them: no clearing needed
+  launch_recon(s->prec, s->eq, a, s->stream);
+  launch_edge(s->prec, s->eq, a, s->stream);
+  HW_CUDA(cudaGetLastError());
+  s->cur = 1 - s->cur;
+  return HW_OK;
+}

@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1}
 EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_ntri", "hw_mesh_neighbors",
             "hw_mesh_permutation", "hw_workspace_bytes", "hw_state_init", "hw_set_state", "hw_step", "hw_run_to",
             "hw_get_state", "hw_conservation", "hw_status_flags", "hw_time", "hw_profile", "hw_profile_read",
-            "hw_solver_destroy", "hw_last_error"]
+            "hw_solver_destroy", "hw_last_error", "hw_step_static_scratch"]
 
 
 class HwError(RuntimeError):
@@ -73,6 +73,7 @@ def load():
         "hw_profile_read": (ctypes.c_int, [vp, vp, P(i64)]),
         "hw_solver_destroy": (ctypes.c_int, [vp]),
         "hw_last_error": (ctypes.c_char_p, []),
+        "hw_step_static_scratch": (ctypes.c_int, [vp, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -181,6 +182,11 @@ class Solver:
 
     def step(self, dt=0.0):
         _check(load().hw_step(self.h, float(dt)))
+
+    def step_static_scratch(self, dt=0.0):
+        """hw_step with the step's scratch in the library's static device array
+        (for callers that cannot allocate device memory; see include/hweno.h)."""
+        _check(load().hw_step_static_scratch(self.h, float(dt)))
 
     def run_to(self, T):
         n = ctypes.c_int64()
