@@ -43,14 +43,15 @@ struct Layout {
 
 Layout make_layout(int64_t N, int m, int prec) {
   const size_t s = prec == HW_FP64 ? 8 : 4;
+  const size_t ld = (size_t)padded_cells(N);   // plane stride
   Layout L{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
-  L.rgeo = take((size_t)NRGEO * N * s);
-  L.igeo = take((size_t)NIGEO * N * 4);
-  L.U0 = take((size_t)3 * m * N * s);
-  L.U1 = take((size_t)3 * m * N * s);
-  L.Pb = take((size_t)18 * m * N * s);
+  L.rgeo = take((size_t)NRGEO * ld * s);
+  L.igeo = take((size_t)NIGEO * ld * 4);
+  L.U0 = take((size_t)3 * m * ld * s);
+  L.U1 = take((size_t)3 * m * ld * s);
+  L.Pb = take((size_t)18 * m * ld * s);
   L.area = take((size_t)N * 8);
   L.perm = take((size_t)N * 4);
   L.stage = take((size_t)3 * m * N * 8);
@@ -71,12 +72,45 @@ hw_status check_options(const hw_options* o) {
   if (!(o->gamma_lin[0] > 0)) return fail(HW_EINVAL, "gamma_1 must be positive");
   return HW_OK;
 }
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// 2-D TMA descriptor over `rows` planes of N cells with plane stride ld
+// elements; box = kCells cells x all rows; out-of-range cells read as zero.
+hw_status encode_planes(CUtensorMap* map, CUtensorMapDataType dt, size_t esize, void* base, int64_t N, int rows,
+                        int64_t ld) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return fail(HW_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+  const cuuint32_t box[2] = {(cuuint32_t)kCells, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HW_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+  return HW_OK;
+}
 }  // namespace
 
 struct hw_solver {
   hw_options opt;
   int prec = 0, eq = 0, m = 1;
   int64_t N = 0;
+  int64_t ld = 0;  // plane stride (cells, multiple of kCells)
+  TensorMaps maps{};
   char* ws = nullptr;
   Layout L{};
   int cur = 0;  // index of the current state buffer
@@ -97,6 +131,10 @@ struct hw_solver {
     a.rgeo = ws + L.rgeo;
     a.igeo = reinterpret_cast<const int32_t*>(ws + L.igeo);
     a.N = (int)N;
+    a.ld = (int)ld;
+    a.from = from;
+    a.maps = &maps;
+    a.tiles = TileSet{nullptr, (int)((N + kCells - 1) / kCells)};
     a.U = U(from);
     a.Un = U(1 - from);
     a.Pb = ws + L.Pb;
@@ -173,8 +211,8 @@ static hw_status upload_state(hw_solver* s, const double* W, const double* V, co
   HW_CUDA(cudaMemcpyAsync(stage, W, plane, cudaMemcpyHostToDevice, s->stream));
   HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + plane, V, plane, cudaMemcpyHostToDevice, s->stream));
   HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + 2 * plane, Y, plane, cudaMemcpyHostToDevice, s->stream));
-  launch_scatter(s->prec, stage, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, 3 * s->m,
-                 s->U(s->cur), s->stream);
+  launch_scatter(s->prec, stage, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld,
+                 3 * s->m, s->U(s->cur), s->stream);
   launch_reset(s->sc(), t, s->opt.cfl, s->stream);
   launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
   HW_CUDA(cudaGetLastError());
@@ -196,6 +234,7 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
   s->eq = opt->eq;
   s->m = ncomp(opt->eq);
   s->N = M.nt;
+  s->ld = padded_cells(M.nt);
   s->L = make_layout(M.nt, s->m, precision);
   if (workspace_bytes < s->L.total) { delete s; return fail(HW_ENOMEM, "workspace smaller than hw_workspace_bytes"); }
   s->ws = static_cast<char*>(workspace);
@@ -205,24 +244,39 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
       cudaMallocHost(&s->h_sc, sizeof(DevScalars)) != cudaSuccess ||
       cudaMallocHost(&s->h_consv, 4 * sizeof(double)) != cudaSuccess)
     return bail(fail(HW_ECUDA, "stream / pinned host buffer creation failed"));
-  // geometry in the solver precision
-  const size_t nr = (size_t)NRGEO * M.nt;
+  // geometry in the solver precision, planes of stride ld
+  const size_t es = precision == HW_FP64 ? 8 : 4;
+  const size_t nt = (size_t)M.nt, ld = (size_t)s->ld;
   cudaError_t e;
   if (precision == HW_FP64) {
-    e = cudaMemcpyAsync(s->ws + s->L.rgeo, M.rgeo.data(), nr * 8, cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpy2DAsync(s->ws + s->L.rgeo, ld * 8, M.rgeo.data(), nt * 8, nt * 8, NRGEO, cudaMemcpyHostToDevice,
+                          s->stream);
   } else {
-    std::vector<float> tmp(nr);
-    for (size_t k = 0; k < nr; ++k) tmp[k] = (float)M.rgeo[k];
-    e = cudaMemcpyAsync(s->ws + s->L.rgeo, tmp.data(), nr * 4, cudaMemcpyHostToDevice, s->stream);
+    std::vector<float> tmp((size_t)NRGEO * nt);
+    for (size_t k = 0; k < tmp.size(); ++k) tmp[k] = (float)M.rgeo[k];
+    e = cudaMemcpy2DAsync(s->ws + s->L.rgeo, ld * 4, tmp.data(), nt * 4, nt * 4, NRGEO, cudaMemcpyHostToDevice,
+                          s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   }
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->ws + s->L.igeo, M.igeo.data(), (size_t)NIGEO * M.nt * 4, cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpy2DAsync(s->ws + s->L.igeo, ld * 4, M.igeo.data(), nt * 4, nt * 4, NIGEO, cudaMemcpyHostToDevice,
+                          s->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->ws + s->L.area, M.area.data(), (size_t)M.nt * 8, cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpyAsync(s->ws + s->L.area, M.area.data(), nt * 8, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->ws + s->L.perm, M.perm.data(), (size_t)M.nt * 4, cudaMemcpyHostToDevice, s->stream);
+    e = cudaMemcpyAsync(s->ws + s->L.perm, M.perm.data(), nt * 4, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return bail(fail(HW_ECUDA, std::string("geometry upload: ") + cudaGetErrorString(e)));
+  // TMA descriptors of the workspace
+  const CUtensorMapDataType dt = precision == HW_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const int m = s->m;
+  hw_status st = encode_planes(&s->maps.geo, dt, es, s->ws + s->L.rgeo, M.nt, kReconPlanes, s->ld);
+  (void)m;
+  if (st == HW_OK)
+    st = encode_planes(&s->maps.egeo, dt, es, s->ws + s->L.rgeo + (size_t)G_NRM * ld * es, M.nt, kEdgePlanes, s->ld);
+  if (st == HW_OK)
+    st = encode_planes(&s->maps.idx, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, s->ws + s->L.igeo, M.nt, NIGEO, s->ld);
+  if (st != HW_OK) return bail(st);
+  prepare_step_kernels(precision, s->eq);
   s->cur = 0;
   if (hw_status st = upload_state(s, Wbar, Vbar, Ybar, 0.0)) return bail(st);
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
@@ -302,8 +356,8 @@ hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, d
   if (!s) return fail(HW_EINVAL, "null solver");
   const size_t plane = (size_t)s->m * s->N * sizeof(double);
   double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
-  launch_gather(s->prec, s->U(s->cur), reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, 3 * s->m,
-                stage, s->stream);
+  launch_gather(s->prec, s->U(s->cur), reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld,
+                3 * s->m, stage, s->stream);
   HW_CUDA(cudaGetLastError());
   if (Wbar) HW_CUDA(cudaMemcpyAsync(Wbar, stage, plane, cudaMemcpyDeviceToHost, s->stream));
   if (Vbar) HW_CUDA(cudaMemcpyAsync(Vbar, reinterpret_cast<char*>(stage) + plane, plane, cudaMemcpyDeviceToHost, s->stream));
@@ -318,8 +372,8 @@ hw_status hw_conservation(hw_solver* s, double* sums) {
   if (!s || !sums) return fail(HW_EINVAL, "null pointer");
   double* partial = reinterpret_cast<double*>(s->ws + s->L.partial);
   double* out = reinterpret_cast<double*>(s->ws + s->L.consv);
-  launch_consv(s->prec, s->U(s->cur), reinterpret_cast<const double*>(s->ws + s->L.area), (int)s->N, s->m, partial,
-               out, s->stream);
+  launch_consv(s->prec, s->U(s->cur), reinterpret_cast<const double*>(s->ws + s->L.area), (int)s->N, (int)s->ld,
+               s->m, partial, out, s->stream);
   HW_CUDA(cudaGetLastError());
   HW_CUDA(cudaMemcpyAsync(s->h_consv, out, s->m * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   HW_CUDA(cudaStreamSynchronize(s->stream));
@@ -429,7 +483,7 @@ hw_status static_scratch_address(void** out) {
 
 extern "C" hw_status hw_step_static_scratch(hw_solver* s, double dt) {
   if (!s) return fail(HW_EINVAL, "null solver");
-  const size_t need = (size_t)18 * s->m * s->N * (s->prec == HW_FP64 ? 8 : 4);
+  const size_t need = (size_t)18 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4);
   if (need > kStaticScratchBytes)
     return fail(HW_EINVAL, "hw_step_static_scratch: the mesh needs " + std::to_string(need) +
                                " bytes of scratch, more than the static maximum of " +

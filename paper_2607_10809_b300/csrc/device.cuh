@@ -30,11 +30,12 @@ struct EqParams {
 };
 
 template <typename R> struct GeoView {
-  const R* __restrict__ rg;        // [NRGEO][N]
-  const int32_t* __restrict__ ig;  // [NIGEO][N]
-  int N;
-  __device__ __forceinline__ R r(int p, int i) const { return __ldg(rg + (size_t)p * N + i); }
-  __device__ __forceinline__ int32_t n(int p, int i) const { return __ldg(ig + (size_t)p * N + i); }
+  const R* __restrict__ rg;        // [NRGEO][ld]
+  const int32_t* __restrict__ ig;  // [NIGEO][ld]
+  int N;                           // cells
+  int ld;                          // plane stride (multiple of 32 cells)
+  __device__ __forceinline__ R r(int p, int i) const { return __ldg(rg + (size_t)p * ld + i); }
+  __device__ __forceinline__ int32_t n(int p, int i) const { return __ldg(ig + (size_t)p * ld + i); }
 };
 
 constexpr int kEqAdvection = 0, kEqBurgers = 1, kEqEuler = 2;
@@ -90,25 +91,19 @@ __device__ __forceinline__ void nonlinear_weights(float Wave, const float beta[4
 // Steps 1-6 of Section 2.2 for component c of cell i: returns the combined
 // quadratic (Eq. recon) as monomials in the scaled frame of the cell,
 //   q(xi, eta) = q0 + q1 xi + q2 eta + q3 xi^2 + q4 xi eta + q5 eta^2.
-template <typename R, int m>
-__device__ __forceinline__ void reconstruct_component(const GeoView<R>& G, const R* __restrict__ U, int N, int i,
-                                                      const int src[3], int c, const EqParams& P, R q[6]) {
-  const R W0 = U[(size_t)(0 * m + c) * N + i];
-  const R V0 = U[(size_t)(1 * m + c) * N + i];
-  const R Y0 = U[(size_t)(2 * m + c) * N + i];
-  R Wl[3], Vl[3], Yl[3];
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    Wl[l] = U[(size_t)(0 * m + c) * N + src[l]];
-    Vl[l] = U[(size_t)(1 * m + c) * N + src[l]];
-    Yl[l] = U[(size_t)(2 * m + c) * N + src[l]];
-  }
+// GA: accessor of this cell's geometry planes, ga(p) = plane p (see RGeo).
+// W0, V0, Y0: the cell's averages; Wl, Vl, Yl: those of the stencil members
+// K1..K3 (a boundary ghost carries the cell's own values).
+template <typename R, typename GA>
+__device__ __forceinline__ void reconstruct_component(const GA& ga, const R W0, const R V0, const R Y0,
+                                                      const R Wl[3], const R Vl[3], const R Yl[3],
+                                                      const EqParams& P, R q[6]) {
   // Step 1: constrained least squares solved once on the host; here the operator
   R rhs[9];
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     rhs[l] = Wl[l] - W0;
-    const R w = G.r(G_W + l, i);
+    const R w = ga(G_W + l);
     rhs[3 + 2 * l] = V0 + w * (Vl[l] - V0);
     rhs[4 + 2 * l] = Y0 + w * (Yl[l] - Y0);
   }
@@ -117,7 +112,7 @@ __device__ __forceinline__ void reconstruct_component(const GeoView<R>& G, const
   for (int r = 0; r < 5; ++r) {
     R s = 0;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) s += G.r(G_M1 + r * 9 + k, i) * rhs[k];
+    for (int k = 0; k < 9; ++k) s += ga(G_M1 + r * 9 + k) * rhs[k];
     cc[r] = s;
   }
   // Step 2: linear polynomials on {K0, K_l}
@@ -126,8 +121,8 @@ __device__ __forceinline__ void reconstruct_component(const GeoView<R>& G, const
   for (int l = 0; l < 3; ++l)
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      b[l][r] = G.r(G_P + l * 6 + r * 3 + 0, i) * (Wl[l] - W0) + G.r(G_P + l * 6 + r * 3 + 1, i) * Vl[l] +
-                G.r(G_P + l * 6 + r * 3 + 2, i) * Yl[l];
+      b[l][r] = ga(G_P + l * 6 + r * 3 + 0) * (Wl[l] - W0) + ga(G_P + l * 6 + r * 3 + 1) * Vl[l] +
+                ga(G_P + l * 6 + r * 3 + 2) * Yl[l];
   // Step 4 (Eq. smoo1): in the frame scaled by h0 = sqrt|K0| the factors
   // |K0|^|s| cancel the chain-rule factors, leaving the scaled derivatives.
   R beta[4];
@@ -148,7 +143,7 @@ __device__ __forceinline__ void reconstruct_component(const GeoView<R>& G, const
   for (int l = 0; l < 3; ++l) { q1 += al[l] * b[l][0]; q2 += al[l] * b[l][1]; }
   const R q3 = a1 * cc[2], q4 = a1 * cc[3], q5 = a1 * cc[4];
   // the constant parts of p1..p4 all equal Wbar_0 and the coefficients sum to one
-  q[0] = W0 - q3 * G.r(G_MOM, i) - q4 * G.r(G_MOM + 1, i) - q5 * G.r(G_MOM + 2, i);
+  q[0] = W0 - q3 * ga(G_MOM) - q4 * ga(G_MOM + 1) - q5 * ga(G_MOM + 2);
   q[1] = q1; q[2] = q2; q[3] = q3; q[4] = q4; q[5] = q5;
 }
 

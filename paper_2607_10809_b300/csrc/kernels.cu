@@ -1,28 +1,45 @@
 // Kernels of one ADER-HWENO time step on a triangular mesh.
 //
-//   k_recon : per cell, Steps 1-6 of Section 2.2 (Eqs. pxy, smoo1,
-//             nonlinearweight, recon), then at its six edge Gauss points the
+//   k_recon : Steps 1-6 of Section 2.2 (Eqs. pxy, smoo1, nonlinearweight,
+//             recon) per cell, then at its six edge Gauss points the
 //             Lax-Wendroff procedure of Section 2.1; writes the Taylor data
 //             (W, W_t, W_tt) of Eqs. tay / tayext to the edge-point buffer.
-//   k_edge  : per cell (owner computes, no atomics), for its three edges the
-//             local Lax-Friedrichs flux at the Gauss-Lobatto time nodes (Eqs.
-//             fx, flux), evaluated in a canonical orientation so that both
-//             cells of an edge obtain bitwise-identical fluxes; the update of
+//   k_edge  : per cell (owner computes, no atomics), at the six Gauss points
+//             of its edges the local Lax-Friedrichs flux at the Gauss-Lobatto
+//             time nodes (Eqs. fx, flux) in a canonical orientation, so both
+//             cells of an edge obtain bitwise-identical values; the update of
 //             the cell average (Eq. flx) and of the derivative averages by
 //             Green-Gauss from the central values at t_{n+1} (Eqs. derave2d2,
-//             timeflux, taylor2dtime); the CFL step for the next step.
+//             timeflux, taylor2dtime); the CFL step of the next step.
 //   k_cfl, k_consv, k_scatter_state, k_gather_state: CFL step of a state,
-//             FP64 conservation sums, host-order <-> Hilbert-order copies.
+//             FP64 conservation sums, host-order <-> internal-order copies.
+//
+// Layout: geometry and neighbour indices are planes of ld cells; the state
+// (3m values per cell) and the edge-point data (6 points x 3 x m values per
+// cell) are records, one contiguous record per cell, so that a neighbour's
+// data are a few 16-byte vector loads.
+//
+// Both main kernels walk tiles of kCells consecutive (Hilbert-ordered) cells
+// with 6 threads per cell.  A block stages each tile's dense operands
+// (geometry planes and neighbour indices by TMA tensor loads, the tile's own
+// state or edge-point records by bulk copies) in shared memory,
+// double-buffered: the copies of the block's next tile are in flight while the
+// current tile is computed.  Neighbour records are gathered with ordinary
+// vector loads (mostly L2 hits thanks to the Hilbert order).
+#include <cuda.h>
+
 #include <cstdint>
 
 #include "device.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace hw {
 
 namespace {
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000ll); }
 
 // Block-wide min of a positive double, then the last block to finish turns the
 // grid-wide minimum into the next time step (threadfence reduction; no spin).
@@ -63,169 +80,327 @@ __device__ void finish_step(DevScalars* sc, double local_min, double dt_taken, b
     }
     vs->dt = dtn;
     vs->done = done;
-    atomicExch(&sc->lam_min_bits, dbits(__longlong_as_double(0x7ff0000000000000ll)));
+    atomicExch(&sc->lam_min_bits, dbits(dinf()));
     atomicExch(&sc->counter, 0u);
+  }
+}
+
+// n contiguous values src -> dst with 16-byte vector accesses when possible
+// (dst, src 16-byte aligned whenever n * sizeof(R) is a multiple of 16).
+template <typename R, int n> __device__ __forceinline__ void copy_rec(R* dst, const R* src) {
+  if constexpr ((n * sizeof(R)) % 16 == 0) {
+    constexpr int v = n * sizeof(R) / 16;
+#pragma unroll
+    for (int k = 0; k < v; ++k) reinterpret_cast<float4*>(dst)[k] = reinterpret_cast<const float4*>(src)[k];
+  } else {
+#pragma unroll
+    for (int k = 0; k < n; ++k) dst[k] = src[k];
+  }
+}
+
+template <typename R> struct SmemGeo {
+  const R* base;  // [plane][kCells]
+  int lc;
+  __device__ __forceinline__ R operator()(int p) const { return base[p * kCells + lc]; }
+};
+
+// Cells of tile `tile`: [cell0, cell0 + count), cell0 a multiple of kCells.
+__device__ __forceinline__ void tile_range(const TileSet& ts, int N, int tile, int& cell0, int& count) {
+  if (ts.table) {
+    const int2 e = ts.table[tile];
+    cell0 = e.x;
+    count = e.y;
+  } else {
+    cell0 = tile * kCells;
+    count = min(kCells, N - cell0);
   }
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- reconstruction
+template <typename R, int EQ> struct ReconStage {
+  static constexpr int m = EqTraits<EQ>::m;
+  R geo[kReconPlanes][kCells];   // TMA tensor box: planes x cells
+  int32_t idx[4][kCells];        // TMA tensor box
+  R u[kCells][3 * m];            // bulk copy of the tile's state records
+};
+
+template <typename R, int EQ> constexpr size_t recon_smem_bytes() {
+  return 2 * sizeof(ReconStage<R, EQ>) + sizeof(R) * EqTraits<EQ>::m * 6 * kCells + 2 * sizeof(uint64_t) + 128;
+}
+
 template <typename R, int EQ>
-__global__ void __launch_bounds__(128) k_recon(GeoView<R> G, const R* __restrict__ U, R* __restrict__ Pb,
-                                                EqParams P, const DevScalars* __restrict__ sc) {
+__global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUtensorMap mGeo,
+                                                     const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
+                                                     const R* __restrict__ U, R* __restrict__ Pb, EqParams P,
+                                                     DevScalars* sc, TileSet ts) {
   constexpr int m = EqTraits<EQ>::m;
+  using Stage = ReconStage<R, EQ>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  Stage* st = reinterpret_cast<Stage*>(base);
+  R (*qs)[6][kCells] = reinterpret_cast<R (*)[6][kCells]>(base + 2 * sizeof(Stage));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * m * 6 * kCells);
+
   if (*(volatile const int*)&sc->done) return;
-  const int N = G.N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  int src[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int nb = G.n(I_NBR + j, i);
-    src[j] = nb >= 0 ? nb : i;   // transmissive ghost carries the cell's own data
+  const int N = G.N, ld = G.ld;
+  const int ntiles = ts.ntiles;
+  const int t = threadIdx.x;
+  constexpr unsigned kBytes = sizeof(Stage);
+  auto issue = [&](int s, int tile) {
+    int c0, cnt;
+    tile_range(ts, N, tile, c0, cnt);
+    mbar_arrive_expect_tx(&bar[s], kBytes);
+    tma_load_2d(&st[s].geo[0][0], &mGeo, c0, 0, &bar[s]);
+    tma_load_2d(&st[s].idx[0][0], &mIdx, c0, 0, &bar[s]);
+    bulk_load(&st[s].u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+  };
+  if (t == 0) {
+    prefetch_tensormap(&mGeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    if ((int)blockIdx.x < ntiles) issue(0, blockIdx.x);
   }
-  R q[m][6];
-#pragma unroll
-  for (int c = 0; c < m; ++c) reconstruct_component<R, m>(G, U, N, i, src, c, P, q[c]);
-  const R ih = G.r(G_IH, i);
-  const R ih2 = ih * ih;
-  R Wxx[m], Wxy[m], Wyy[m];
-#pragma unroll
-  for (int c = 0; c < m; ++c) { Wxx[c] = R(2) * q[c][3] * ih2; Wxy[c] = q[c][4] * ih2; Wyy[c] = R(2) * q[c][5] * ih2; }
-  R vx[3], vy[3];
-#pragma unroll
-  for (int v = 0; v < 3; ++v) { vx[v] = G.r(G_VX + 2 * v, i); vy[v] = G.r(G_VX + 2 * v + 1, i); }
-  const R gs[2] = {R(0.5) - R(0.28867513459481288225), R(0.5) + R(0.28867513459481288225)};
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int jn = (j + 1) % 3;
-      const R xi = vx[j] + gs[g] * (vx[jn] - vx[j]);
-      const R et = vy[j] + gs[g] * (vy[jn] - vy[j]);
-      R W[m], Wx[m], Wy[m], Wt[m], Wtt[m];
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        W[c] = q[c][0] + xi * (q[c][1] + q[c][3] * xi + q[c][4] * et) + et * (q[c][2] + q[c][5] * et);
-        Wx[c] = (q[c][1] + R(2) * q[c][3] * xi + q[c][4] * et) * ih;
-        Wy[c] = (q[c][2] + q[c][4] * xi + R(2) * q[c][5] * et) * ih;
+  __syncthreads();
+  unsigned phase0 = 0, phase1 = 0;
+  int s = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s ^= 1) {
+    const int next = tile + gridDim.x;
+    if (t == 0 && next < ntiles) {
+      fence_proxy_async();
+      issue(s ^ 1, next);
+    }
+    const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0);
+    if (s) phase1 ^= 1u; else phase0 ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicOr(&sc->flags, 2u);
+        if (next < ntiles) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1);   // drain the copy in flight
       }
-      lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
-      const int qp = 2 * j + g;
+      return;
+    }
+    int cell0, count;
+    tile_range(ts, N, tile, cell0, count);
+    const Stage& S = st[s];
+    if (t < m * kCells) {
+      const int lc = t % kCells, c = t / kCells;
+      if (lc < count) {
+        R Wl[3], Vl[3], Yl[3];
+        const R* own = S.u[lc];
 #pragma unroll
-      for (int c = 0; c < m; ++c) {
-        Pb[(size_t)((qp * 3 + 0) * m + c) * N + i] = W[c];
-        Pb[(size_t)((qp * 3 + 1) * m + c) * N + i] = Wt[c];
-        Pb[(size_t)((qp * 3 + 2) * m + c) * N + i] = Wtt[c];
+        for (int j = 0; j < 3; ++j) {
+          const int nb = S.idx[j][lc];
+          const R* rec = nb >= 0 ? U + (size_t)nb * 3 * m : own;   // transmissive ghost: own data
+          Wl[j] = rec[0 * m + c]; Vl[j] = rec[1 * m + c]; Yl[j] = rec[2 * m + c];
+        }
+        R q[6];
+        reconstruct_component<R>(SmemGeo<R>{&S.geo[0][0], lc}, own[0 * m + c], own[1 * m + c], own[2 * m + c], Wl, Vl,
+                                 Yl, P, q);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) qs[c][k][lc] = q[k];
       }
     }
+    __syncthreads();
+    {
+      const int lc = t % kCells, qp = t / kCells, i = cell0 + lc;
+      if (lc < count) {
+        const int j = qp >> 1, g = qp & 1, jn = (j + 1) % 3;
+        const R sg = g == 0 ? R(0.5) - R(0.28867513459481288225) : R(0.5) + R(0.28867513459481288225);
+        const R xi = S.geo[G_VX + 2 * j][lc] + sg * (S.geo[G_VX + 2 * jn][lc] - S.geo[G_VX + 2 * j][lc]);
+        const R et = S.geo[G_VX + 2 * j + 1][lc] + sg * (S.geo[G_VX + 2 * jn + 1][lc] - S.geo[G_VX + 2 * j + 1][lc]);
+        const R ih = S.geo[G_IH][lc], ih2 = ih * ih;
+        R W[m], Wx[m], Wy[m], Wxx[m], Wxy[m], Wyy[m], Wt[m], Wtt[m];
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          const R q0 = qs[c][0][lc], q1 = qs[c][1][lc], q2 = qs[c][2][lc];
+          const R q3 = qs[c][3][lc], q4 = qs[c][4][lc], q5 = qs[c][5][lc];
+          W[c] = q0 + xi * (q1 + q3 * xi + q4 * et) + et * (q2 + q5 * et);
+          Wx[c] = (q1 + R(2) * q3 * xi + q4 * et) * ih;
+          Wy[c] = (q2 + q4 * xi + R(2) * q5 * et) * ih;
+          Wxx[c] = R(2) * q3 * ih2; Wxy[c] = q4 * ih2; Wyy[c] = R(2) * q5 * ih2;
+        }
+        lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
+        R rec[3 * m];
+#pragma unroll
+        for (int c = 0; c < m; ++c) { rec[c] = W[c]; rec[m + c] = Wt[c]; rec[2 * m + c] = Wtt[c]; }
+        copy_rec<R, 3 * m>(Pb + (size_t)i * 18 * m + qp * 3 * m, rec);
+      }
+    }
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------- flux + update
+template <typename R, int EQ> struct EdgeStage {
+  static constexpr int m = EqTraits<EQ>::m;
+  R geo[kEdgePlanes][kCells];    // TMA tensor box: planes x cells
+  int32_t idx[4][kCells];        // TMA tensor box
+  R pb[kCells][18 * m];          // bulk copy of the tile's edge-point records
+  R u[kCells][3 * m];            // bulk copy of the tile's state records
+};
+
+template <typename R, int EQ> constexpr size_t edge_smem_bytes() {
+  return 2 * sizeof(EdgeStage<R, EQ>) + sizeof(R) * 3 * EqTraits<EQ>::m * 6 * kCells + 2 * sizeof(uint64_t) + 128;
+}
+
 template <typename R, int EQ>
-__global__ void __launch_bounds__(128) k_edge(GeoView<R> G, const R* __restrict__ U, R* __restrict__ Un,
-                                               const R* __restrict__ Pb, EqParams P, DevScalars* sc,
-                                               double dt_fixed) {
+__global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUtensorMap mEgeo,
+                                                    const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
+                                                    const R* __restrict__ U, R* __restrict__ Un,
+                                                    const R* __restrict__ Pb, EqParams P, DevScalars* sc,
+                                                    double dt_fixed, TileSet ts) {
   constexpr int m = EqTraits<EQ>::m;
-  const int N = G.N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  using Stage = EdgeStage<R, EQ>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  Stage* st = reinterpret_cast<Stage*>(base);
+  R (*part)[m][6][kCells] = reinterpret_cast<R (*)[m][6][kCells]>(base + 2 * sizeof(Stage));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells);
+
+  const int N = G.N, ld = G.ld;
+  const int ntiles = ts.ntiles;
+  const int t = threadIdx.x;
   const volatile DevScalars* vs = sc;
-  if (vs->done) {
-    if (i < N)
-      for (int k = 0; k < 3 * m; ++k) Un[(size_t)k * N + i] = U[(size_t)k * N + i];
+  if (vs->done) {  // target reached: keep the state, preserving the buffer alternation
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      int cell0, count;
+      tile_range(ts, N, tile, cell0, count);
+      for (int k = t; k < 3 * m * count; k += kThreads) Un[(size_t)cell0 * 3 * m + k] = U[(size_t)cell0 * 3 * m + k];
+    }
     return;
   }
   const double dt = dt_fixed > 0 ? dt_fixed : vs->dt;
-  double local_min = __longlong_as_double(0x7ff0000000000000ll);
-  if (i < N) {
-    const R dtr = R(dt);
-    const R tau[3] = {R(0), R(0.5) * dtr, dtr};
-    const R wts[3] = {R(1.0 / 6.0), R(4.0 / 6.0), R(1.0 / 6.0)};
-    R Wi[m];
-#pragma unroll
-    for (int c = 0; c < m; ++c) Wi[c] = U[(size_t)c * N + i];
-    const int packed = G.n(I_NBE, i);
-    R Racc[m], GV[m], GY[m];
-#pragma unroll
-    for (int c = 0; c < m; ++c) { Racc[c] = R(0); GV[c] = R(0); GY[c] = R(0); }
-#pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
-      const int nb = G.n(I_NBR + j, i);
-      const int je = (packed >> (2 * j)) & 3;
-      const bool left = (nb < 0) || (i < nb);
-      const R nx = G.r(G_NRM + 2 * j, i), ny = G.r(G_NRM + 2 * j + 1, i);
-      const R el = G.r(G_EL + j, i);
-      R Wn[m];
-#pragma unroll
-      for (int c = 0; c < m; ++c) Wn[c] = nb >= 0 ? U[(size_t)c * N + nb] : Wi[c];
-      R WbL[m], WbR[m];
-#pragma unroll
-      for (int c = 0; c < m; ++c) { WbL[c] = left ? Wi[c] : Wn[c]; WbR[c] = left ? Wn[c] : Wi[c]; }
-      const R aL = spectral_radius_n<R, EQ>(WbL, nx, ny, P), aR = spectral_radius_n<R, EQ>(WbR, nx, ny, P);
-      const R alpha = aL > aR ? aL : aR;
-      // cells and point indices of the two sides, left side's Gauss-point order
-      const int cl = left ? i : nb, cr = left ? (nb >= 0 ? nb : i) : i;
-      const int el_ = left ? j : je;                              // left cell's local edge
-      const int er_ = left ? (nb >= 0 ? je : j) : j;              // right cell's local edge
-      R Fe[m], Se[m];
-#pragma unroll
-      for (int c = 0; c < m; ++c) { Fe[c] = R(0); Se[c] = R(0); }
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const int ql = 2 * el_ + g;
-        const int qr = (nb >= 0) ? 2 * er_ + (1 - g) : ql;        // boundary: W^ext = W^int
+  const R dtr = R(dt);
+  constexpr unsigned kBytes = sizeof(Stage);
+  auto issue = [&](int s, int tile) {
+    int c0, cnt;
+    tile_range(ts, N, tile, c0, cnt);
+    mbar_arrive_expect_tx(&bar[s], kBytes);
+    tma_load_2d(&st[s].geo[0][0], &mEgeo, c0, 0, &bar[s]);
+    tma_load_2d(&st[s].idx[0][0], &mIdx, c0, 0, &bar[s]);
+    bulk_load(&st[s].pb[0][0], Pb + (size_t)c0 * 18 * m, kCells * 18 * m * sizeof(R), &bar[s]);
+    bulk_load(&st[s].u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+  };
+  if (t == 0) {
+    prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    if ((int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+  }
+  __syncthreads();
+  double local_min = dinf();
+  unsigned phase0 = 0, phase1 = 0;
+  int s = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s ^= 1) {
+    const int next = tile + gridDim.x;
+    if (t == 0 && next < ntiles) {
+      fence_proxy_async();
+      issue(s ^ 1, next);
+    }
+    const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0);
+    if (s) phase1 ^= 1u; else phase0 ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicOr(&sc->flags, 2u);
+        if (next < ntiles) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1);
+      }
+      local_min = dinf();
+      break;
+    }
+    int cell0, count;
+    tile_range(ts, N, tile, cell0, count);
+    const Stage& S = st[s];
+    {
+      const int lc = t % kCells, qp = t / kCells, i = cell0 + lc;
+      if (lc < count) {
+        const int j = qp >> 1, gm = qp & 1;
+        const int nb = S.idx[j][lc];
+        const int je = (S.idx[3][lc] >> (2 * j)) & 3;
+        const bool left = (nb < 0) || (i < nb);
+        const R nx = S.geo[2 * j][lc], ny = S.geo[2 * j + 1][lc];
+        const R el = S.geo[6 + j][lc];
+        R Wi[m], Wn[m];
+        copy_rec<R, m>(Wi, S.u[lc]);
+        if (nb >= 0) copy_rec<R, m>(Wn, U + (size_t)nb * 3 * m);
+        else copy_rec<R, m>(Wn, Wi);
+        R aL, aR;
+        if (left) { aL = spectral_radius_n<R, EQ>(Wi, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wn, nx, ny, P); }
+        else      { aL = spectral_radius_n<R, EQ>(Wn, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wi, nx, ny, P); }
+        const R alpha = aL > aR ? aL : aR;
+        // this cell's Taylor data at its point (j, gm); the neighbour's at the
+        // same physical point, its point (je, 1 - gm); canonical left / right
+        const int qm = 2 * j + gm, qn = 2 * je + (1 - gm);
+        R mine[3 * m], theirs[3 * m];
+        copy_rec<R, 3 * m>(mine, &S.pb[lc][qm * 3 * m]);
+        if (nb >= 0) copy_rec<R, 3 * m>(theirs, Pb + (size_t)nb * 18 * m + qn * 3 * m);
+        else copy_rec<R, 3 * m>(theirs, mine);   // boundary: W^ext = W^int
         R a0[m], a1[m], a2[m], b0[m], b1[m], b2[m];
 #pragma unroll
         for (int c = 0; c < m; ++c) {
-          a0[c] = Pb[(size_t)((ql * 3 + 0) * m + c) * N + cl];
-          a1[c] = Pb[(size_t)((ql * 3 + 1) * m + c) * N + cl];
-          a2[c] = Pb[(size_t)((ql * 3 + 2) * m + c) * N + cl];
-          b0[c] = Pb[(size_t)((qr * 3 + 0) * m + c) * N + cr];
-          b1[c] = Pb[(size_t)((qr * 3 + 1) * m + c) * N + cr];
-          b2[c] = Pb[(size_t)((qr * 3 + 2) * m + c) * N + cr];
+          a0[c] = left ? mine[c] : theirs[c];
+          a1[c] = left ? mine[m + c] : theirs[m + c];
+          a2[c] = left ? mine[2 * m + c] : theirs[2 * m + c];
+          b0[c] = left ? theirs[c] : mine[c];
+          b1[c] = left ? theirs[m + c] : mine[m + c];
+          b2[c] = left ? theirs[2 * m + c] : mine[2 * m + c];
         }
+        const R tau[3] = {R(0), R(0.5) * dtr, dtr};
+        const R wts[3] = {R(1.0 / 6.0), R(4.0 / 6.0), R(1.0 / 6.0)};
+        R Fe[m], Sh[m];
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
+        for (int c = 0; c < m; ++c) Fe[c] = R(0);
+#pragma unroll
+        for (int si = 0; si < 3; ++si) {
           R WL[m], WR[m], HL[m], HR[m];
-          const R hs = R(0.5) * tau[s] * tau[s];
+          const R hs = R(0.5) * tau[si] * tau[si];
 #pragma unroll
           for (int c = 0; c < m; ++c) {
-            WL[c] = a0[c] + tau[s] * a1[c] + hs * a2[c];
-            WR[c] = b0[c] + tau[s] * b1[c] + hs * b2[c];
+            WL[c] = a0[c] + tau[si] * a1[c] + hs * a2[c];
+            WR[c] = b0[c] + tau[si] * b1[c] + hs * b2[c];
           }
           flux_n<R, EQ>(WL, nx, ny, P, HL);
           flux_n<R, EQ>(WR, nx, ny, P, HR);
 #pragma unroll
-          for (int c = 0; c < m; ++c) Fe[c] += wts[s] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
-          if (s == 2) {
+          for (int c = 0; c < m; ++c) Fe[c] += wts[si] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
+          if (si == 2) {
 #pragma unroll
-            for (int c = 0; c < m; ++c) Se[c] += R(0.5) * (WL[c] + WR[c]);
+            for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
           }
         }
+        // Gauss weight 1/2 and the cell's outward normal (+-n)
+        const R sgn = left ? R(0.5) * el : R(-0.5) * el;
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          part[0][c][qp][lc] = sgn * Fe[c];
+          part[1][c][qp][lc] = sgn * nx * Sh[c];
+          part[2][c][qp][lc] = sgn * ny * Sh[c];
+        }
       }
-      // two Gauss points of weight 1/2; the cell's outward normal is +-n
-      const R sg = left ? R(0.5) * el : R(-0.5) * el;
+    }
+    __syncthreads();
+    if (t < count) {
+      const int i = cell0 + t;
+      R Wnew[m], out[3 * m];
 #pragma unroll
       for (int c = 0; c < m; ++c) {
-        Racc[c] += sg * Fe[c];
-        GV[c] += sg * nx * Se[c];
-        GY[c] += sg * ny * Se[c];
+        R r = R(0), gv = R(0), gy = R(0);
+#pragma unroll
+        for (int qp = 0; qp < 6; ++qp) { r += part[0][c][qp][t]; gv += part[1][c][qp][t]; gy += part[2][c][qp][t]; }
+        Wnew[c] = S.u[t][c] - dtr * r;
+        out[c] = Wnew[c]; out[m + c] = gv; out[2 * m + c] = gy;
+      }
+      copy_rec<R, 3 * m>(Un + (size_t)i * 3 * m, out);
+      if (!physical<R, EQ>(Wnew, P)) atomicOr(&sc->flags, 1u);
+      const double lam = spectral_radius_all<R, EQ>(Wnew, P);
+      if (lam > 0) {
+        const double v = (double)S.geo[G_INR - G_NRM][t] / lam;
+        if (v >= 0 && v < local_min) local_min = v;
       }
     }
-    R Wnew[m];
-#pragma unroll
-    for (int c = 0; c < m; ++c) {
-      Wnew[c] = Wi[c] - dtr * Racc[c];
-      Un[(size_t)(0 * m + c) * N + i] = Wnew[c];
-      Un[(size_t)(1 * m + c) * N + i] = GV[c];
-      Un[(size_t)(2 * m + c) * N + i] = GY[c];
-    }
-    if (!physical<R, EQ>(Wnew, P)) atomicOr(&sc->flags, 1u);
-    const double lam = spectral_radius_all<R, EQ>(Wnew, P);
-    if (lam > 0) local_min = (double)G.r(G_INR, i) / lam;
-    if (!(local_min >= 0)) local_min = __longlong_as_double(0x7ff0000000000000ll);
+    __syncthreads();
   }
   finish_step(sc, local_min, dt, true);
 }
@@ -234,17 +409,17 @@ __global__ void __launch_bounds__(128) k_edge(GeoView<R> G, const R* __restrict_
 template <typename R, int EQ>
 __global__ void __launch_bounds__(256) k_cfl(GeoView<R> G, const R* __restrict__ U, EqParams P, DevScalars* sc) {
   constexpr int m = EqTraits<EQ>::m;
-  const int N = G.N;
+  const int N = G.N, ld = G.ld;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double local_min = __longlong_as_double(0x7ff0000000000000ll);
+  double local_min = dinf();
   if (i < N) {
     R W[m];
 #pragma unroll
-    for (int c = 0; c < m; ++c) W[c] = U[(size_t)c * N + i];
+    for (int c = 0; c < m; ++c) W[c] = U[(size_t)i * 3 * m + c];
     if (!physical<R, EQ>(W, P)) atomicOr(&sc->flags, 1u);
     const double lam = spectral_radius_all<R, EQ>(W, P);
     if (lam > 0) local_min = (double)G.r(G_INR, i) / lam;
-    if (!(local_min >= 0)) local_min = __longlong_as_double(0x7ff0000000000000ll);
+    if (!(local_min >= 0)) local_min = dinf();
   }
   finish_step(sc, local_min, 0.0, false);
 }
@@ -252,12 +427,12 @@ __global__ void __launch_bounds__(256) k_cfl(GeoView<R> G, const R* __restrict__
 // Deterministic FP64 sums of |K| Wbar_K: fixed grid, fixed tree, then one block.
 template <typename R>
 __global__ void __launch_bounds__(256) k_consv_partial(const R* __restrict__ U, const double* __restrict__ area, int N,
-                                                        int m, double* __restrict__ partial) {
+                                                        int ld, int m, double* __restrict__ partial) {
   __shared__ double sh[256];
   for (int c = 0; c < m; ++c) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-      s += area[i] * (double)U[(size_t)c * N + i];
+      s += area[i] * (double)U[(size_t)i * 3 * m + c];
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -278,22 +453,22 @@ __global__ void k_consv_final(const double* __restrict__ partial, int nparts, in
     }
 }
 
-// host order (double) -> internal order (R), and back
+// host order (double, [planes][N]) -> internal order (R, [planes][ld]), and back
 template <typename R>
-__global__ void k_scatter_state(const double* __restrict__ host_order, const int32_t* __restrict__ perm, int N,
+__global__ void k_scatter_state(const double* __restrict__ host_order, const int32_t* __restrict__ perm, int N, int ld,
                                 int planes, R* __restrict__ U) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int src = perm[i];
-  for (int k = 0; k < planes; ++k) U[(size_t)k * N + i] = (R)host_order[(size_t)k * N + src];
+  for (int k = 0; k < planes; ++k) U[(size_t)i * planes + k] = (R)host_order[(size_t)k * N + src];
 }
 template <typename R>
-__global__ void k_gather_state(const R* __restrict__ U, const int32_t* __restrict__ perm, int N, int planes,
+__global__ void k_gather_state(const R* __restrict__ U, const int32_t* __restrict__ perm, int N, int ld, int planes,
                                double* __restrict__ host_order) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int dst = perm[i];
-  for (int k = 0; k < planes; ++k) host_order[(size_t)k * N + dst] = (double)U[(size_t)k * N + i];
+  for (int k = 0; k < planes; ++k) host_order[(size_t)k * N + dst] = (double)U[(size_t)i * planes + k];
 }
 
 __global__ void k_reset(DevScalars* sc, double t, double cfl) {
@@ -319,18 +494,49 @@ __global__ void k_set_target(DevScalars* sc, double T, int has_T) {
 
 // ---------------------------------------------------------------- launchers
 namespace {
+// Resident blocks of a kernel on the current device (occupancy x SMs); the
+// launches use min(tiles, this) blocks.
+template <typename K> int resident_blocks(K kernel, size_t smem) {
+  int dev = 0, sms = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <typename R, int EQ> int recon_cap() {
+  static const int cap = resident_blocks(k_recon<R, EQ>, recon_smem_bytes<R, EQ>());
+  return cap;
+}
+template <typename R, int EQ> int edge_cap() {
+  static const int cap = resident_blocks(k_edge<R, EQ>, edge_smem_bytes<R, EQ>());
+  return cap;
+}
+template <typename R, int EQ> void prepare_t() {
+  (void)recon_cap<R, EQ>();
+  (void)edge_cap<R, EQ>();
+}
+
 template <typename R, int EQ> void launch_recon_t(const StepArgs& a, cudaStream_t st) {
-  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N};
-  k_recon<R, EQ><<<(a.N + 127) / 128, 128, 0, st>>>(G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb),
-                                                     a.P, a.sc);
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
+  constexpr size_t smem = recon_smem_bytes<R, EQ>();
+  const int cap = recon_cap<R, EQ>();
+  const int nt = a.tiles.ntiles;
+  k_recon<R, EQ><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
+      a.maps->geo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb), a.P, a.sc, a.tiles);
 }
 template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
-  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N};
-  k_edge<R, EQ><<<(a.N + 127) / 128, 128, 0, st>>>(G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
-                                                    reinterpret_cast<const R*>(a.Pb), a.P, a.sc, a.dt_fixed);
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
+  constexpr size_t smem = edge_smem_bytes<R, EQ>();
+  const int cap = edge_cap<R, EQ>();
+  const int nt = a.tiles.ntiles;
+  k_edge<R, EQ><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
+      a.maps->egeo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
+      reinterpret_cast<const R*>(a.Pb), a.P, a.sc, a.dt_fixed, a.tiles);
 }
 template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t st) {
-  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N};
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
   k_cfl<R, EQ><<<(a.N + 255) / 256, 256, 0, st>>>(G, reinterpret_cast<const R*>(a.U), a.P, a.sc);
 }
 }  // namespace
@@ -348,13 +554,13 @@ template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t 
     }                                                  \
   } while (0)
 
+void prepare_step_kernels(int prec, int eq) { HW_DISPATCH(prepare_t, prec, eq); }
 void launch_recon(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_recon_t, prec, eq, a, st); }
 void launch_edge(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_edge_t, prec, eq, a, st); }
 void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st) {
   launch_recon(prec, eq, a, st);
   launch_edge(prec, eq, a, st);
 }
-
 void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_cfl_t, prec, eq, a, st); }
 
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st) { k_reset<<<1, 32, 0, st>>>(sc, t, cfl); }
@@ -363,34 +569,31 @@ void launch_set_target(DevScalars* sc, double T, int has_T, cudaStream_t st) {
   k_set_target<<<1, 32, 0, st>>>(sc, T, has_T);
 }
 
-void launch_consv(int prec, const void* U, const double* area, int N, int m, double* partial, double* out,
+void launch_consv(int prec, const void* U, const double* area, int N, int ld, int m, double* partial, double* out,
                   cudaStream_t st) {
-  if (prec == 0) k_consv_partial<double><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const double*>(U), area, N, m, partial);
-  else k_consv_partial<float><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const float*>(U), area, N, m, partial);
+  if (prec == 0)
+    k_consv_partial<double><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const double*>(U), area, N, ld, m, partial);
+  else
+    k_consv_partial<float><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const float*>(U), area, N, ld, m, partial);
   k_consv_final<<<1, 32, 0, st>>>(partial, kConsvBlocks, m, out);
 }
 
-void launch_scatter(int prec, const double* host_order, const int32_t* perm, int N, int planes, void* U,
+void launch_scatter(int prec, const double* host_order, const int32_t* perm, int N, int ld, int planes, void* U,
                     cudaStream_t st) {
   const int nb = (N + 255) / 256;
-  if (prec == 0) k_scatter_state<double><<<nb, 256, 0, st>>>(host_order, perm, N, planes, reinterpret_cast<double*>(U));
-  else k_scatter_state<float><<<nb, 256, 0, st>>>(host_order, perm, N, planes, reinterpret_cast<float*>(U));
+  if (prec == 0)
+    k_scatter_state<double><<<nb, 256, 0, st>>>(host_order, perm, N, ld, planes, reinterpret_cast<double*>(U));
+  else
+    k_scatter_state<float><<<nb, 256, 0, st>>>(host_order, perm, N, ld, planes, reinterpret_cast<float*>(U));
 }
 
-void launch_gather(int prec, const void* U, const int32_t* perm, int N, int planes, double* host_order,
+void launch_gather(int prec, const void* U, const int32_t* perm, int N, int ld, int planes, double* host_order,
                    cudaStream_t st) {
   const int nb = (N + 255) / 256;
-  if (prec == 0) k_gather_state<double><<<nb, 256, 0, st>>>(reinterpret_cast<const double*>(U), perm, N, planes, host_order);
-  else k_gather_state<float><<<nb, 256, 0, st>>>(reinterpret_cast<const float*>(U), perm, N, planes, host_order);
-}
-
-// geometry rounding (FP64 host precompute -> device precision)
-__global__ void k_round_geo(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-    dst[k] = (float)src[k];
-}
-void launch_round_geo(const double* src, float* dst, size_t n, cudaStream_t st) {
-  k_round_geo<<<1184, 256, 0, st>>>(src, dst, n);
+  if (prec == 0)
+    k_gather_state<double><<<nb, 256, 0, st>>>(reinterpret_cast<const double*>(U), perm, N, ld, planes, host_order);
+  else
+    k_gather_state<float><<<nb, 256, 0, st>>>(reinterpret_cast<const float*>(U), perm, N, ld, planes, host_order);
 }
 
 }  // namespace hw
