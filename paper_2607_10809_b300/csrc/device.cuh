@@ -270,18 +270,19 @@ __device__ __forceinline__ R spectral_radius_n(const R* W, R nx, R ny, const EqP
   }
 }
 
-// Spectral radius over all directions (CFL time step).
+// Spectral radius over all directions (CFL time step), in the working
+// precision R.
 template <typename R, int EQ>
-__device__ __forceinline__ double spectral_radius_all(const R* W, const EqParams& P) {
+__device__ __forceinline__ R spectral_radius_all(const R* W, const EqParams& P) {
   if constexpr (EQ == kEqAdvection) {
-    return sqrt(P.ax * P.ax + P.ay * P.ay);
+    return R(sqrt(P.ax * P.ax + P.ay * P.ay));
   } else if constexpr (EQ == kEqBurgers) {
-    return 1.4142135623730951 * fabs((double)W[0]);
+    return R(1.4142135623730951) * fabs(W[0]);
   } else {
-    const double r = W[0], mx = W[1], my = W[2], E = W[3];
-    const double u = mx / r, v = my / r;
-    const double p = (P.gam - 1.0) * (E - 0.5 * (mx * u + my * v));
-    return sqrt(u * u + v * v) + sqrt(P.gam * p / r);
+    const R ir = R(1) / W[0];
+    const R u = W[1] * ir, v = W[2] * ir;
+    const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
+    return sqrt(u * u + v * v) + sqrt(R(P.gam) * p * ir);
   }
 }
 

@@ -242,7 +242,8 @@ template <typename R, int EQ> struct EdgeStage {
 };
 
 template <typename R, int EQ> constexpr size_t edge_smem_bytes() {
-  return 2 * sizeof(EdgeStage<R, EQ>) + sizeof(R) * 3 * EqTraits<EQ>::m * 6 * kCells + 2 * sizeof(uint64_t) + 128;
+  return 2 * sizeof(EdgeStage<R, EQ>) + sizeof(R) * 3 * EqTraits<EQ>::m * 6 * kCells +
+         sizeof(R) * EqTraits<EQ>::m * kCells + 2 * sizeof(uint64_t) + 128;
 }
 
 template <typename R, int EQ>
@@ -257,7 +258,9 @@ __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUten
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*part)[m][6][kCells] = reinterpret_cast<R (*)[m][6][kCells]>(base + 2 * sizeof(Stage));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells);
+  R (*wn)[kCells] = reinterpret_cast<R (*)[kCells]>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells);
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells + sizeof(R) * m * kCells);
 
   const int N = G.N, ld = G.ld;
   const int ntiles = ts.ntiles;
@@ -381,22 +384,31 @@ __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUten
       }
     }
     __syncthreads();
-    if (t < count) {
-      const int i = cell0 + t;
-      R Wnew[m], out[3 * m];
+    // sums of the six shares: thread (cell, output) for the 3m outputs
+    for (int k = t; k < 3 * m * kCells; k += kThreads) {
+      const int lc = k % kCells, o = k / kCells;   // o = kind * m + c
+      if (lc < count) {
+        const int kind = o / m, c = o % m;
+        R r = R(0);
 #pragma unroll
-      for (int c = 0; c < m; ++c) {
-        R r = R(0), gv = R(0), gy = R(0);
-#pragma unroll
-        for (int qp = 0; qp < 6; ++qp) { r += part[0][c][qp][t]; gv += part[1][c][qp][t]; gy += part[2][c][qp][t]; }
-        Wnew[c] = S.u[t][c] - dtr * r;
-        out[c] = Wnew[c]; out[m + c] = gv; out[2 * m + c] = gy;
+        for (int qp = 0; qp < 6; ++qp) r += part[kind][c][qp][lc];
+        R v = r;
+        if (kind == 0) {
+          v = S.u[lc][c] - dtr * r;
+          wn[c][lc] = v;
+        }
+        Un[(size_t)(cell0 + lc) * 3 * m + o] = v;
       }
-      copy_rec<R, 3 * m>(Un + (size_t)i * 3 * m, out);
+    }
+    __syncthreads();
+    if (t < count) {
+      R Wnew[m];
+#pragma unroll
+      for (int c = 0; c < m; ++c) Wnew[c] = wn[c][t];
       if (!physical<R, EQ>(Wnew, P)) atomicOr(&sc->flags, 1u);
-      const double lam = spectral_radius_all<R, EQ>(Wnew, P);
-      if (lam > 0) {
-        const double v = (double)S.geo[G_INR - G_NRM][t] / lam;
+      const R lam = spectral_radius_all<R, EQ>(Wnew, P);
+      if (lam > R(0)) {
+        const double v = (double)(S.geo[G_INR - G_NRM][t] / lam);
         if (v >= 0 && v < local_min) local_min = v;
       }
     }
@@ -417,8 +429,8 @@ __global__ void __launch_bounds__(256) k_cfl(GeoView<R> G, const R* __restrict__
 #pragma unroll
     for (int c = 0; c < m; ++c) W[c] = U[(size_t)i * 3 * m + c];
     if (!physical<R, EQ>(W, P)) atomicOr(&sc->flags, 1u);
-    const double lam = spectral_radius_all<R, EQ>(W, P);
-    if (lam > 0) local_min = (double)G.r(G_INR, i) / lam;
+    const R lam = spectral_radius_all<R, EQ>(W, P);
+    if (lam > R(0)) local_min = (double)(G.r(G_INR, i) / lam);
     if (!(local_min >= 0)) local_min = dinf();
   }
   finish_step(sc, local_min, 0.0, false);
