@@ -63,7 +63,12 @@ typedef enum { HW_BC_PERIODIC = 0, HW_BC_TRANSMISSIVE = 1 } hw_bc;
  * (Step 5), CFL 0.5 (Section 3), gamma 1.4 (Example 3.2). */
 typedef struct {
   int32_t eq;           /* hw_equation */
-  int32_t reserved0;
+  int32_t positivity;   /* Euler only: 1 = apply the scale limiter of Zhang and Shu
+                           (Section 3 uses it "in some extreme cases"): the
+                           reconstruction and its space-time Taylor data are
+                           pulled toward the cell average so that density and
+                           pressure stay >= min(1e-13, rho_bar, p_bar) at the six
+                           edge Gauss points and the three time nodes; 0 = off */
   double ax, ay;        /* advection velocity (HW_ADVECTION) */
   double gamma_gas;     /* ratio of specific heats (HW_EULER) */
   double cfl;           /* dt = cfl * min_K inradius_K / lambda_K */

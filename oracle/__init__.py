@@ -44,6 +44,7 @@ def lib():
         _lib.orc_create.argtypes = [vp, i64, vp, i64, d, d, ctypes.c_int, ctypes.c_int, d, d, d, d, vp, d,
                                     ctypes.c_int, P(vp)]
         _lib.orc_destroy.argtypes = [vp]
+        _lib.orc_set_positivity.argtypes = [vp, ctypes.c_int]
         _lib.orc_neighbors.argtypes = [vp, vp, vp]
         _lib.orc_cell_geometry.argtypes = [vp, vp]
         _lib.orc_cfl_dt.argtypes = [vp, vp]
@@ -53,6 +54,7 @@ def lib():
         _lib.orc_run_dual.argtypes = [vp, vp, vp, vp, i64]
         _lib.orc_reconstruct_cell.argtypes = [vp, vp, i64, ctypes.c_int, vp, vp, vp, vp, vp]
         _lib.orc_lax_wendroff.argtypes = [ctypes.c_int, d, d, d, vp, vp]
+        _lib.orc_cell_taylor.argtypes = [vp, vp, d, i64, vp]
         _lib.orc_flux_derivs.argtypes = [ctypes.c_int, d, d, d, vp, vp, vp, vp]
         _lib.orc_last_error.restype = ctypes.c_char_p
     return _lib
@@ -71,7 +73,8 @@ class Oracle:
     """One mesh + equation.  All arrays are float64 in the caller's numbering."""
 
     def __init__(self, mesh, eq: str = "advection", a=(1.0, 1.0), gamma_gas: float = 1.4, cfl: float = 0.5,
-                 gamma_lin=(0.94, 0.02, 0.02, 0.02), eps: float = 1e-8, linear_only: bool = False):
+                 gamma_lin=(0.94, 0.02, 0.02, 0.02), eps: float = 1e-8, linear_only: bool = False,
+                 positivity: bool = False):
         L = lib()
         self.mesh = mesh
         self.eq = EQ[eq]
@@ -85,6 +88,8 @@ class Oracle:
                             self.eq, a[0], a[1], gamma_gas, cfl, _ptr(self._gl), eps, int(linear_only),
                             ctypes.byref(h)))
         self._h = h
+        if positivity:
+            _check(L.orc_set_positivity(h, 1))
         self.a = a
         self.gamma_gas = gamma_gas
 
@@ -140,6 +145,14 @@ class Oracle:
         dts = np.ascontiguousarray(dts, dtype=np.float64)
         _check(lib().orc_run_dual(self._h, _ptr(U), _ptr(dU), _ptr(dts), len(dts)))
         return U, dU
+
+    def cell_taylor(self, U, dt, cell: int):
+        """Taylor data (W, Wt, Wtt) at the six edge Gauss points of a cell,
+        after the limiter when it is on -> [6, 3, m]."""
+        U = self._u(U)
+        out = np.empty((6, 3, self.m))
+        _check(lib().orc_cell_taylor(self._h, _ptr(U), float(dt), int(cell), _ptr(out)))
+        return out
 
     def reconstruct_cell(self, U, cell: int, comp: int = 0):
         U = self._u(U)

@@ -115,6 +115,7 @@ struct Params {
   double glin[4];   // linear weights gamma_1..gamma_4 (Step 3)
   double eps;       // epsilon of Eq. nonlinearweight (1e-8)
   int linear_only;  // debug: replace nonlinear weights by the linear ones
+  int positivity;   // scale limiter of Zhang and Shu on the reconstruction (R18)
 };
 
 struct EdgeRec {
@@ -315,6 +316,9 @@ void basis_means(const double* X, const double* Y, double M3, double M4, double 
 template <class S> struct CellRecon {
   Poly<S> p[4];      // p1 (quadratic), p2, p3, p4 (linear)
   S beta[4], omega[4];
+  S wbar;            // cell average of the component
+  S theta;           // spatial scale factor of the limiter (1: unchanged)
+  S theta_t;         // scale factor of the limiter on the time Taylor data (1: unchanged)
   bool ok;
 };
 
@@ -354,6 +358,9 @@ void stencil_member(const Problem& pb, int64_t t, int l, double X[3], double Y[3
 template <class S> CellRecon<S> reconstruct(const Problem& pb, const S* U, int64_t t, int c) {
   CellRecon<S> R;
   R.ok = true;
+  R.theta = S(1.0);
+  R.theta_t = S(1.0);
+  R.wbar = Uat(U, pb, 0, c, t);
   const double x0 = pb.cx[t], y0 = pb.cy[t], A0 = pb.area[t], h0 = std::sqrt(A0);
   // scaled vertices of K0 and its second moments
   double X0[3], Y0[3];
@@ -480,6 +487,8 @@ template <class S> CellRecon<S> reconstruct(const Problem& pb, const S* U, int64
   return R;
 }
 
+const double kGLpt = 0.28867513459481288225;  // sqrt(3)/6: Gauss-Legendre points at 1/2 -+ kGLpt
+
 // ---- Step 6 (Eq. recon): value and derivatives of the final reconstruction at
 // the point (x, y) of t's frame, evaluated polynomial by polynomial.
 template <class S> void recon_at(const CellRecon<S>& R, const double* g, double x, double y, S out[6]) {
@@ -492,6 +501,84 @@ template <class S> void recon_at(const CellRecon<S>& R, const double* g, double 
     for (int l = 1; l < 4; ++l) o = o + R.omega[l] * v[l][d];
     out[d] = o;
   }
+  // scale limiter: W~ = Wbar + theta (W - Wbar), derivatives scaled by theta
+  if (val(R.theta) != 1.0) {
+    out[0] = R.wbar + R.theta * (out[0] - R.wbar);
+    for (int d = 1; d < 6; ++d) out[d] = R.theta * out[d];
+  }
+}
+
+// Pressure of a conservative state (Eq. 2d equation of state).
+template <class S> S pressure(double gam, const S* W) {
+  return S(gam - 1.0) * (W[3] - S(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+}
+
+// Smallest non-negative root, clamped to 1, of the pressure condition along
+// the segment Wb + f d: (gam-1) [(E0 + f dE)(r0 + f dr) - |m0 + f dm|^2 / 2]
+// - eps (r0 + f dr) = a f^2 + b f + c0 = 0 (R18).  Clamping makes the factor
+// tend to 1 as the point value approaches the admissible boundary.
+template <class S> S pressure_root(double gam, const S Wb[4], const S d[4], double eps) {
+  const S g1 = S(gam - 1.0);
+  const S a = g1 * (d[3] * d[0] - S(0.5) * (d[1] * d[1] + d[2] * d[2]));
+  const S b = g1 * (Wb[3] * d[0] + Wb[0] * d[3] - (Wb[1] * d[1] + Wb[2] * d[2])) - S(eps) * d[0];
+  const S c0 = g1 * (Wb[3] * Wb[0] - S(0.5) * (Wb[1] * Wb[1] + Wb[2] * Wb[2])) - S(eps) * Wb[0];
+  S tk = S(0.0);
+  if (std::fabs(val(a)) < 1e-300) {
+    if (val(b) < 0) tk = S(0.0) - c0 / b;
+    if (val(tk) > 1) tk = S(1.0);
+  } else {
+    const S disc = b * b - S(4.0) * a * c0;
+    const S sq = val(disc) > 0 ? sqrt(disc) : S(0.0);
+    const S r1 = (S(0.0) - b - sq) / (S(2.0) * a), r2 = (S(0.0) - b + sq) / (S(2.0) * a);
+    S best = S(-1.0);
+    if (val(r1) >= 0) best = r1;
+    if (val(r2) >= 0 && (val(best) < 0 || val(r2) < val(best))) best = r2;
+    tk = val(best) < 0 ? S(0.0) : (val(best) > 1 ? S(1.0) : best);
+  }
+  return tk;
+}
+
+// Positivity-preserving scaling of Zhang and Shu (the "scale limiter" of
+// Section 3), applied to the final reconstruction of one Euler cell (R18):
+// over the six edge Gauss points, first scale the density part around its
+// cell average so that it stays >= eps, then scale all components so that the
+// pressure stays >= eps, eps = min(1e-13, rho_bar, p_bar).
+template <class S> void positivity_scaling(const Problem& pb, CellRecon<S>* rec, int64_t t) {
+  const double gam = pb.P.gam;
+  S Wb[4];
+  for (int c = 0; c < 4; ++c) Wb[c] = rec[c].wbar;
+  const S pb0 = pressure(gam, Wb);
+  if (!(val(Wb[0]) > 0) || !(val(pb0) > 0)) return;  // the average itself is not admissible
+  const double eps = std::min(1e-13, std::min(val(Wb[0]), val(pb0)));
+  S q[6][4];
+  for (int j = 0; j < 3; ++j)
+    for (int gi = 0; gi < 2; ++gi) {
+      const double s = (gi == 0) ? 0.5 - kGLpt : 0.5 + kGLpt;
+      const double Ax = pb.vx[3 * t + j], Ay = pb.vy[3 * t + j];
+      const double Bx = pb.vx[3 * t + (j + 1) % 3], By = pb.vy[3 * t + (j + 1) % 3];
+      for (int c = 0; c < 4; ++c) {
+        S o[6];
+        recon_at(rec[c], pb.P.glin, Ax + s * (Bx - Ax), Ay + s * (By - Ay), o);
+        q[2 * j + gi][c] = o[0];
+      }
+    }
+  // density
+  S rmin = q[0][0];
+  for (int k = 1; k < 6; ++k) if (val(q[k][0]) < val(rmin)) rmin = q[k][0];
+  S th1 = S(1.0);
+  if (val(rmin) < eps) th1 = (Wb[0] - S(eps)) / (Wb[0] - rmin);
+  // pressure along the segment from the average to each limited point value
+  S th2 = S(1.0);
+  for (int k = 0; k < 6; ++k) {
+    S w[4] = {Wb[0] + th1 * (q[k][0] - Wb[0]), q[k][1], q[k][2], q[k][3]};
+    if (val(pressure(gam, w)) >= eps) continue;
+    S d[4];
+    for (int c = 0; c < 4; ++c) d[c] = w[c] - Wb[c];
+    const S tk = pressure_root(gam, Wb, d, eps);
+    if (val(tk) < val(th2)) th2 = tk;
+  }
+  rec[0].theta = th1 * th2;
+  for (int c = 1; c < 4; ++c) rec[c].theta = th2;
 }
 
 // ------------------------------------------------------------------ fluxes
@@ -600,6 +687,56 @@ void side_taylor(const Problem& pb, const CellRecon<S>* rec, double x, double y,
   S Wtx[4], Wty[4];
   lax_wendroff(pb.P, J, Wt, Wtx, Wty, Wtt);
   for (int c = 0; c < m; ++c) W[c] = J[0][c];
+  // limiter on the space-time Taylor data (R18): scale toward the average
+  if (val(rec[0].theta_t) != 1.0)
+    for (int c = 0; c < m; ++c) {
+      W[c] = rec[c].wbar + rec[c].theta_t * (W[c] - rec[c].wbar);
+      Wt[c] = rec[c].theta_t * Wt[c];
+      Wtt[c] = rec[c].theta_t * Wtt[c];
+    }
+}
+
+// Largest f in [0, 1] with rho, p >= eps on Wb + f (w - Wb): density first,
+// then pressure through the quadratic in f (R18).
+template <class S> S admissible_fraction(double gam, const S Wb[4], const S w[4], double eps) {
+  S f1 = S(1.0);
+  if (val(w[0]) < eps) f1 = (Wb[0] - S(eps)) / (Wb[0] - w[0]);
+  S d[4];
+  for (int c = 0; c < 4; ++c) d[c] = f1 * (w[c] - Wb[c]);
+  S v[4];
+  for (int c = 0; c < 4; ++c) v[c] = Wb[c] + d[c];
+  if (val(pressure(gam, v)) >= eps) return f1;
+  const S tk = pressure_root(gam, Wb, d, eps);
+  return f1 * tk;
+}
+
+// Limiter on the space-time data of one Euler cell: the Taylor values at its
+// six edge Gauss points and the three Lobatto time nodes are pulled toward the
+// cell average by one common factor so that rho, p >= eps at all of them.
+template <class S> void positivity_time_scaling(const Problem& pb, CellRecon<S>* rec, int64_t t, double dt) {
+  const double gam = pb.P.gam;
+  S Wb[4];
+  for (int c = 0; c < 4; ++c) Wb[c] = rec[c].wbar;
+  const S pb0 = pressure(gam, Wb);
+  if (!(val(Wb[0]) > 0) || !(val(pb0) > 0)) return;
+  const double eps = std::min(1e-13, std::min(val(Wb[0]), val(pb0)));
+  S th = S(1.0);
+  for (int j = 0; j < 3; ++j)
+    for (int gi = 0; gi < 2; ++gi) {
+      const double s = (gi == 0) ? 0.5 - kGLpt : 0.5 + kGLpt;
+      const double Ax = pb.vx[3 * t + j], Ay = pb.vy[3 * t + j];
+      const double Bx = pb.vx[3 * t + (j + 1) % 3], By = pb.vy[3 * t + (j + 1) % 3];
+      S W[4], Wt[4], Wtt[4];
+      side_taylor(pb, rec, Ax + s * (Bx - Ax), Ay + s * (By - Ay), W, Wt, Wtt);
+      for (int si = 0; si < 3; ++si) {
+        const double tau = kTau[si] * dt;
+        S w[4];
+        for (int c = 0; c < 4; ++c) w[c] = W[c] + Wt[c] * S(tau) + Wtt[c] * S(0.5 * tau * tau);
+        const S f = admissible_fraction(gam, Wb, w, eps);
+        if (val(f) < val(th)) th = f;
+      }
+    }
+  for (int c = 0; c < 4; ++c) rec[c].theta_t = th;
 }
 
 // One time step.  If `mask` is non-null only cells with mask[i] != 0 are
@@ -627,6 +764,10 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
     for (int c = 0; c < m; ++c) {
       rec[slot[i] * m + c] = reconstruct(pb, U, i, c);
       if (!rec[slot[i] * m + c].ok) { g_err = "singular reconstruction system"; return 4; }
+    }
+    if (pb.P.positivity && pb.P.eq == EQ_EULER) {
+      positivity_scaling(pb, &rec[slot[i] * m], i);
+      positivity_time_scaling(pb, &rec[slot[i] * m], i, dt);
     }
   }
   std::vector<S> Rf(nt * m, S(0.0)), GV(nt * m, S(0.0)), GY(nt * m, S(0.0));
@@ -730,7 +871,7 @@ int orc_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt, dou
   pb->P.eq = eq; pb->P.m = (eq == EQ_EULER) ? 4 : 1;
   pb->P.ax = ax; pb->P.ay = ay; pb->P.gam = gam; pb->P.cfl = cfl;
   for (int l = 0; l < 4; ++l) pb->P.glin[l] = glin ? glin[l] : (l == 0 ? 0.94 : 0.02);
-  pb->P.eps = eps; pb->P.linear_only = linear_only;
+  pb->P.eps = eps; pb->P.linear_only = linear_only; pb->P.positivity = 0;
   for (int64_t i = 0; i < 3 * nt; ++i)
     if (tri[i] < 0 || tri[i] >= nv) { g_err = "vertex index out of range"; delete pb; return 4; }
   if (!build_connectivity(*pb, tri) || !build_geometry(*pb, xy, tri)) { delete pb; return 4; }
@@ -739,6 +880,12 @@ int orc_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt, dou
 }
 
 void orc_destroy(orc_problem* p) { delete reinterpret_cast<Problem*>(p); }
+
+// Switch the scale limiter (R18) on or off.
+int orc_set_positivity(orc_problem* p, int on) {
+  reinterpret_cast<Problem*>(p)->P.positivity = on;
+  return 0;
+}
 
 int orc_neighbors(const orc_problem* p, int32_t* nbr, int32_t* nbe) {
   const Problem* pb = reinterpret_cast<const Problem*>(p);
@@ -833,6 +980,37 @@ int orc_reconstruct_cell(const orc_problem* p, const double* U, int64_t t, int c
       for (int d = 0; d < 6; ++d) recon[q * 6 + d] = o[d];
     }
   for (int l = 0; l < 4; ++l) { beta[l] = R.beta[l]; omega[l] = R.omega[l]; }
+  return 0;
+}
+
+// Taylor data (W, Wt, Wtt) at the six edge Gauss points of cell t for a step
+// of size dt, after the limiter when it is on: out[6][3][m].
+int orc_cell_taylor(const orc_problem* p, const double* U, double dt, int64_t t, double* out) {
+  const Problem* pb = reinterpret_cast<const Problem*>(p);
+  const int m = pb->P.m;
+  std::vector<CellRecon<double>> rec(m);
+  for (int c = 0; c < m; ++c) {
+    rec[c] = reconstruct<double>(*pb, U, t, c);
+    if (!rec[c].ok) { g_err = "singular reconstruction system"; return 4; }
+  }
+  if (pb->P.positivity && pb->P.eq == EQ_EULER) {
+    positivity_scaling(*pb, rec.data(), t);
+    positivity_time_scaling(*pb, rec.data(), t, dt);
+  }
+  for (int j = 0; j < 3; ++j)
+    for (int gi = 0; gi < 2; ++gi) {
+      const double s = (gi == 0) ? 0.5 - kGL : 0.5 + kGL;
+      const double Ax = pb->vx[3 * t + j], Ay = pb->vy[3 * t + j];
+      const double Bx = pb->vx[3 * t + (j + 1) % 3], By = pb->vy[3 * t + (j + 1) % 3];
+      double W[4], Wt[4], Wtt[4];
+      side_taylor(*pb, rec.data(), Ax + s * (Bx - Ax), Ay + s * (By - Ay), W, Wt, Wtt);
+      const int q = 2 * j + gi;
+      for (int c = 0; c < m; ++c) {
+        out[(q * 3 + 0) * m + c] = W[c];
+        out[(q * 3 + 1) * m + c] = Wt[c];
+        out[(q * 3 + 2) * m + c] = Wtt[c];
+      }
+    }
   return 0;
 }
 

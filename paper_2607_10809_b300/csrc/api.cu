@@ -70,6 +70,7 @@ hw_status check_options(const hw_options* o) {
   if (!(o->cfl > 0)) return fail(HW_EINVAL, "cfl must be positive");
   if (o->eq == HW_EULER && !(o->gamma_gas > 1)) return fail(HW_EINVAL, "gamma_gas must exceed 1");
   if (!(o->gamma_lin[0] > 0)) return fail(HW_EINVAL, "gamma_1 must be positive");
+  if (o->positivity != 0 && o->positivity != 1) return fail(HW_EINVAL, "positivity must be 0 or 1");
   return HW_OK;
 }
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -141,6 +142,7 @@ struct hw_solver {
     a.sc = sc();
     a.dt_fixed = dt_fixed;
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
+    a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
     for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
     return a;
   }

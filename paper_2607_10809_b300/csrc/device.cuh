@@ -27,6 +27,7 @@ struct DevScalars {
 struct EqParams {
   double ax, ay, gam, eps;
   double g[4];
+  int positivity;   // scale limiter on (Euler)
 };
 
 template <typename R> struct GeoView {
@@ -284,6 +285,48 @@ __device__ __forceinline__ R spectral_radius_all(const R* W, const EqParams& P) 
     const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
     return sqrt(u * u + v * v) + sqrt(R(P.gam) * p * ir);
   }
+}
+
+// Scale limiter (Zhang and Shu), Euler.  Pressure of a conservative state.
+template <typename R> __device__ __forceinline__ R pressure_of(R gam, const R* W) {
+  return (gam - R(1)) * (W[3] - R(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+}
+
+// Smallest root in [0, 1] of p(Wb + f d) = eps (times the density, a
+// quadratic in f); 0 if none.
+template <typename R> __device__ __forceinline__ R pressure_root(R gam, const R Wb[4], const R d[4], R eps) {
+  const R g1 = gam - R(1);
+  const R a = g1 * (d[3] * d[0] - R(0.5) * (d[1] * d[1] + d[2] * d[2]));
+  const R b = g1 * (Wb[3] * d[0] + Wb[0] * d[3] - (Wb[1] * d[1] + Wb[2] * d[2])) - eps * d[0];
+  const R c0 = g1 * (Wb[3] * Wb[0] - R(0.5) * (Wb[1] * Wb[1] + Wb[2] * Wb[2])) - eps * Wb[0];
+  R tk = R(0);
+  if (fabs(a) < R(sizeof(R) == 8 ? 1e-300 : 1e-37)) {
+    if (b < R(0)) tk = -c0 / b;
+    if (tk > R(1)) tk = R(1);
+  } else {
+    const R disc = b * b - R(4) * a * c0;
+    const R sq = disc > R(0) ? sqrt(disc) : R(0);
+    const R r1 = (-b - sq) / (R(2) * a), r2 = (-b + sq) / (R(2) * a);
+    // smallest non-negative root, clamped to 1 (continuous at the boundary)
+    R best = R(-1);
+    if (r1 >= R(0)) best = r1;
+    if (r2 >= R(0) && (best < R(0) || r2 < best)) best = r2;
+    tk = best < R(0) ? R(0) : (best > R(1) ? R(1) : best);
+  }
+  return tk;
+}
+
+// Largest f in [0, 1] such that Wb + f (w - Wb) has density and pressure >= eps:
+// density first, then the pressure root.
+template <typename R>
+__device__ __forceinline__ R admissible_fraction(R gam, const R Wb[4], const R w[4], R eps) {
+  R f1 = R(1);
+  if (w[0] < eps) f1 = (Wb[0] - eps) / (Wb[0] - w[0]);
+  R d[4], v[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { d[c] = f1 * (w[c] - Wb[c]); v[c] = Wb[c] + d[c]; }
+  if (pressure_of(gam, v) >= eps) return f1;
+  return f1 * pressure_root(gam, Wb, d, eps);
 }
 
 template <typename R, int EQ> __device__ __forceinline__ bool physical(const R* W, const EqParams& P) {

@@ -127,23 +127,26 @@ template <typename R, int EQ> struct ReconStage {
 };
 
 template <typename R, int EQ> constexpr size_t recon_smem_bytes() {
-  return 2 * sizeof(ReconStage<R, EQ>) + sizeof(R) * EqTraits<EQ>::m * 6 * kCells + 2 * sizeof(uint64_t) + 128;
+  return 2 * sizeof(ReconStage<R, EQ>) + sizeof(R) * (EqTraits<EQ>::m + 1) * 6 * kCells + 2 * sizeof(uint64_t) + 128;
 }
 
-template <typename R, int EQ>
+template <typename R, int EQ, bool LIM>
 __global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUtensorMap mGeo,
                                                      const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
                                                      const R* __restrict__ U, R* __restrict__ Pb, EqParams P,
-                                                     DevScalars* sc, TileSet ts) {
+                                                     DevScalars* sc, double dt_fixed, TileSet ts) {
   constexpr int m = EqTraits<EQ>::m;
   using Stage = ReconStage<R, EQ>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*qs)[6][kCells] = reinterpret_cast<R (*)[6][kCells]>(base + 2 * sizeof(Stage));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * m * 6 * kCells);
+  R (*lim)[kCells] = reinterpret_cast<R (*)[kCells]>(base + 2 * sizeof(Stage) + sizeof(R) * m * 6 * kCells);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * (m + 1) * 6 * kCells);
 
-  if (*(volatile const int*)&sc->done) return;
+  const volatile DevScalars* vsc = sc;
+  if (vsc->done) return;
+  const R dtr = R(dt_fixed > 0 ? dt_fixed : vsc->dt);   // time nodes of the limiter
   const int N = G.N, ld = G.ld;
   const int ntiles = ts.ntiles;
   const int t = threadIdx.x;
@@ -205,13 +208,14 @@ __global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUte
     __syncthreads();
     {
       const int lc = t % kCells, qp = t / kCells, i = cell0 + lc;
-      if (lc < count) {
+      const bool act = lc < count;
+      R W[m], Wx[m], Wy[m], Wxx[m], Wxy[m], Wyy[m], Wt[m], Wtt[m];
+      if (act) {
         const int j = qp >> 1, g = qp & 1, jn = (j + 1) % 3;
         const R sg = g == 0 ? R(0.5) - R(0.28867513459481288225) : R(0.5) + R(0.28867513459481288225);
         const R xi = S.geo[G_VX + 2 * j][lc] + sg * (S.geo[G_VX + 2 * jn][lc] - S.geo[G_VX + 2 * j][lc]);
         const R et = S.geo[G_VX + 2 * j + 1][lc] + sg * (S.geo[G_VX + 2 * jn + 1][lc] - S.geo[G_VX + 2 * j + 1][lc]);
         const R ih = S.geo[G_IH][lc], ih2 = ih * ih;
-        R W[m], Wx[m], Wy[m], Wxx[m], Wxy[m], Wyy[m], Wt[m], Wtt[m];
 #pragma unroll
         for (int c = 0; c < m; ++c) {
           const R q0 = qs[c][0][lc], q1 = qs[c][1][lc], q2 = qs[c][2][lc];
@@ -221,7 +225,83 @@ __global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUte
           Wy[c] = (q2 + q4 * xi + R(2) * q5 * et) * ih;
           Wxx[c] = R(2) * q3 * ih2; Wxy[c] = q4 * ih2; Wyy[c] = R(2) * q5 * ih2;
         }
+      }
+      if constexpr (EQ == kEqEuler && LIM) {
+        {
+          // scale limiter (block-uniform branch): spatial scaling over the six
+          // Gauss points, then the Lax-Wendroff data, then scaling of the
+          // space-time Taylor data over the points and the three time nodes
+          const R gam = R(P.gam);
+          R Wb[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) Wb[c] = S.u[lc][c];
+          const R pb0 = act ? pressure_of(gam, Wb) : R(0);
+          const bool ok = act && Wb[0] > R(0) && pb0 > R(0);
+          const R eps = ok ? fmin(R(1e-13), fmin(Wb[0], pb0)) : R(0);
+          if (act) lim[qp][lc] = W[0];
+          __syncthreads();
+          R th1 = R(1), th2 = R(1);
+          if (ok) {
+            R rmin = lim[0][lc];
+#pragma unroll
+            for (int k = 1; k < 6; ++k) rmin = lim[k][lc] < rmin ? lim[k][lc] : rmin;
+            if (rmin < eps) th1 = (Wb[0] - eps) / (Wb[0] - rmin);
+          }
+          __syncthreads();
+          R f = R(1);
+          if (ok) {
+            R w[4] = {Wb[0] + th1 * (W[0] - Wb[0]), W[1], W[2], W[3]};
+            if (pressure_of(gam, w) < eps) {
+              R d[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) d[c] = w[c] - Wb[c];
+              f = pressure_root(gam, Wb, d, eps);
+            }
+          }
+          if (act) lim[qp][lc] = f;
+          __syncthreads();
+          if (ok) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) th2 = lim[k][lc] < th2 ? lim[k][lc] : th2;
+          }
+          __syncthreads();
+          if (ok && (th1 != R(1) || th2 != R(1))) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const R th = c == 0 ? th1 * th2 : th2;
+              W[c] = Wb[c] + th * (W[c] - Wb[c]);
+              Wx[c] *= th; Wy[c] *= th; Wxx[c] *= th; Wxy[c] *= th; Wyy[c] *= th;
+            }
+          }
+          if (act) lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
+          R ft = R(1);
+          if (ok) {
+            const R tau[3] = {R(0), R(0.5) * dtr, dtr};
+#pragma unroll
+            for (int si = 0; si < 3; ++si) {
+              R w[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) w[c] = W[c] + Wt[c] * tau[si] + Wtt[c] * (R(0.5) * tau[si] * tau[si]);
+              const R fs = admissible_fraction(gam, Wb, w, eps);
+              ft = fs < ft ? fs : ft;
+            }
+          }
+          if (act) lim[qp][lc] = ft;
+          __syncthreads();
+          R tht = R(1);
+          if (ok) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) tht = lim[k][lc] < tht ? lim[k][lc] : tht;
+          }
+          if (ok && tht != R(1)) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { W[c] = Wb[c] + tht * (W[c] - Wb[c]); Wt[c] *= tht; Wtt[c] *= tht; }
+          }
+        }
+      } else if (act) {
         lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
+      }
+      if (act) {
         R rec[3 * m];
 #pragma unroll
         for (int c = 0; c < m; ++c) { rec[c] = W[c]; rec[m + c] = Wt[c]; rec[2 * m + c] = Wtt[c]; }
@@ -517,8 +597,8 @@ template <typename K> int resident_blocks(K kernel, size_t smem) {
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-template <typename R, int EQ> int recon_cap() {
-  static const int cap = resident_blocks(k_recon<R, EQ>, recon_smem_bytes<R, EQ>());
+template <typename R, int EQ, bool LIM> int recon_cap() {
+  static const int cap = resident_blocks(k_recon<R, EQ, LIM>, recon_smem_bytes<R, EQ>());
   return cap;
 }
 template <typename R, int EQ> int edge_cap() {
@@ -526,17 +606,28 @@ template <typename R, int EQ> int edge_cap() {
   return cap;
 }
 template <typename R, int EQ> void prepare_t() {
-  (void)recon_cap<R, EQ>();
+  (void)recon_cap<R, EQ, false>();
+  if constexpr (EQ == kEqEuler) (void)recon_cap<R, EQ, true>();
   (void)edge_cap<R, EQ>();
 }
 
-template <typename R, int EQ> void launch_recon_t(const StepArgs& a, cudaStream_t st) {
+template <typename R, int EQ, bool LIM> void launch_recon_lim(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
   constexpr size_t smem = recon_smem_bytes<R, EQ>();
-  const int cap = recon_cap<R, EQ>();
+  const int cap = recon_cap<R, EQ, LIM>();
   const int nt = a.tiles.ntiles;
-  k_recon<R, EQ><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
-      a.maps->geo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb), a.P, a.sc, a.tiles);
+  k_recon<R, EQ, LIM><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
+      a.maps->geo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb), a.P, a.sc,
+      a.dt_fixed, a.tiles);
+}
+template <typename R, int EQ> void launch_recon_t(const StepArgs& a, cudaStream_t st) {
+  if constexpr (EQ == kEqEuler) {
+    if (a.P.positivity) {
+      launch_recon_lim<R, EQ, true>(a, st);
+      return;
+    }
+  }
+  launch_recon_lim<R, EQ, false>(a, st);
 }
 template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};

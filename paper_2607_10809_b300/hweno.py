@@ -35,7 +35,7 @@ class HwError(RuntimeError):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("eq", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("ax", ctypes.c_double),
+    _fields_ = [("eq", ctypes.c_int32), ("positivity", ctypes.c_int32), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("gamma_gas", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("gamma_lin", ctypes.c_double * 4), ("eps", ctypes.c_double)]
 
@@ -92,10 +92,12 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def options(eq="advection", a=(1.0, 1.0), gamma_gas=1.4, cfl=0.5, gamma_lin=(0.94, 0.02, 0.02, 0.02), eps=1e-8):
+def options(eq="advection", a=(1.0, 1.0), gamma_gas=1.4, cfl=0.5, gamma_lin=(0.94, 0.02, 0.02, 0.02), eps=1e-8,
+            positivity=False):
     o = Options()
     load().hw_options_default(ctypes.byref(o))
     o.eq = EQUATIONS[eq]
+    o.positivity = int(bool(positivity))
     o.ax, o.ay = a
     o.gamma_gas = gamma_gas
     o.cfl = cfl

@@ -162,3 +162,23 @@ def test_fp32_error_against_fp64_oracle(case):
     linf = np.abs(Ug[0] - Uo[0]).max(axis=1)
     print(f"FP32 {case}: L1 {l1} Linf {linf} steps {n}")
     assert np.all(l1 < 1e-5) and np.all(linf < 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_euler_riemann_with_scale_limiter(precision):
+    mesh = I.jittered_box(20, seed=4)
+    U0 = I.initial_state(mesh, I.quadrant_fn(I.quadrant_states(4)), 4, nq=4)
+    o = oracle.Oracle(mesh, "euler", positivity=True)
+    Uo, dts = o.run_to(U0, 0.05)
+    s = hweno.Solver(mesh, U0, eq="euler", precision=precision, positivity=True)
+    n = s.run_to(0.05)
+    Ug, t = s.get_state()
+    rho = Ug[0, 0]; p = 0.4 * (Ug[0, 3] - 0.5 * (Ug[0, 1] ** 2 + Ug[0, 2] ** 2) / rho)
+    assert rho.min() > 0 and p.min() > 0
+    if precision == "fp64":
+        assert n == len(dts)
+        assert rel_linf(Ug, Uo) < FP64_TOL
+    else:
+        err = np.abs(Ug[0] - Uo[0]).max(axis=1) / np.abs(Uo[0]).max(axis=1)
+        print("FP32 limited Riemann rel Linf per component", err)
+        assert np.all(err < 1e-3)
