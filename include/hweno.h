@@ -167,6 +167,59 @@ hw_status hw_solver_destroy(hw_solver* s);
  *   - Allocates nothing (no cudaMalloc, cudaFree or allocating library call). */
 hw_status hw_step_static_scratch(hw_solver* s, double dt);
 
+/* ---------------------------------------------------------------------------
+ * Batched runs: many independent solves (same options, meshes of any sizes)
+ * advanced together.  All time steps of all solves run inside one persistent
+ * cooperative kernel launch (captured in a CUDA graph): per step a
+ * reconstruction phase over the tiles of the solves still running, a grid
+ * barrier, the flux/update phase, a barrier, the per-solve time step update
+ * (each solve keeps its own CFL step and time, Section 3), a barrier.  Grid
+ * barriers spin a bounded number of times; on time-out the launch stops and
+ * the next call returns HW_ETIMEOUT.  A solve whose state becomes non-finite
+ * or non-physical is stopped alone (reported by hw_batch_get_state) while the
+ * others continue. */
+typedef struct hw_batch hw_batch;
+typedef struct {
+  int32_t blocks_per_sm;     /* blocks of the persistent launch per SM; 0 = as many as fit */
+  int32_t tile_order;        /* 0 solve by solve, 1 largest solves first, 2 round robin over solves */
+  int32_t steps_per_launch;  /* time steps per launch (graph replay) at most */
+  int32_t withhold_block;    /* testing only: this block withholds its first barrier arrival (-1: none) */
+  int64_t spin_limit;        /* polls of a barrier wait before giving up; 0 = default (about 2 s) */
+} hw_batch_schedule;
+
+void hw_batch_schedule_default(hw_batch_schedule* s);
+/* Workspace bytes of a batch of n meshes (same options / precision as hw_state_init). */
+hw_status hw_batch_workspace_bytes(const hw_mesh* const* meshes, int32_t n, const hw_options* opt, int32_t precision,
+                                   size_t* bytes);
+/* Upload the n meshes' geometry and initial states (host arrays per solve, as
+ * for hw_state_init) into the caller's workspace; t = 0 for every solve.
+ * The meshes may be destroyed afterwards.  Synchronises. */
+hw_status hw_batch_create(const hw_mesh* const* meshes, int32_t n, const hw_options* opt, int32_t precision,
+                          const double* const* Wbar, const double* const* Vbar, const double* const* Ybar,
+                          void* workspace, size_t workspace_bytes, void* cuda_stream, hw_batch** out);
+hw_status hw_batch_set_schedule(hw_batch* b, const hw_batch_schedule* s);
+/* Current schedule and the grid it launches (blocks). */
+hw_status hw_batch_get_schedule(const hw_batch* b, hw_batch_schedule* s, int32_t* grid_blocks);
+/* Time every candidate schedule (tile order x blocks per SM) on trial_steps
+ * steps from the initial state, keep the fastest, restore the initial state.
+ * best / best_ms may be NULL. */
+hw_status hw_batch_autotune(hw_batch* b, int32_t trial_steps, hw_batch_schedule* best, double* best_ms);
+/* Advance every solve to time T (each with its own CFL steps, the last one
+ * clipped to T); synchronises.  cell_steps (may be NULL): sum over solves of
+ * triangles x steps taken.  HW_ENONFINITE if a solve failed (the others are
+ * still advanced), HW_ETIMEOUT if a barrier wait gave up. */
+hw_status hw_batch_run_to(hw_batch* b, double T, int64_t* cell_steps);
+/* Exactly `steps` steps of every running solve in one launch (no target
+ * time), timed with CUDA events (ms may be NULL); synchronises. */
+hw_status hw_batch_steps(hw_batch* b, int32_t steps, double* ms);
+/* Back to the initial states and t = 0. */
+hw_status hw_batch_reset(hw_batch* b);
+/* State of one solve in its caller numbering (as hw_get_state), its time, steps
+ * and failure flag; any output may be NULL.  Synchronises. */
+hw_status hw_batch_get_state(hw_batch* b, int32_t solve, double* Wbar, double* Vbar, double* Ybar, double* t,
+                             int64_t* nsteps, int32_t* failed);
+hw_status hw_batch_destroy(hw_batch* b);
+
 /* Message of the last failing call on this thread. */
 const char* hw_last_error(void);
 

@@ -15,10 +15,6 @@
 
 using namespace hw;
 
-struct hw_mesh {
-  HostMesh M;
-};
-
 namespace {
 thread_local std::string g_last_error;
 
@@ -105,6 +101,18 @@ hw_status encode_planes(CUtensorMap* map, CUtensorMapDataType dt, size_t esize, 
   return HW_OK;
 }
 }  // namespace
+
+void hw_set_last_error_internal(const char* msg) { g_last_error = msg ? msg : ""; }
+
+// TMA descriptors of the geometry and index planes (shared with batches).
+hw_status hw_encode_plane_maps(TensorMaps* maps, int precision, char* rgeo, char* igeo, int64_t N, int64_t ld) {
+  const size_t es = precision == HW_FP64 ? 8 : 4;
+  const CUtensorMapDataType dt = precision == HW_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  hw_status st = encode_planes(&maps->geo, dt, es, rgeo, N, kReconPlanes, ld);
+  if (st == HW_OK) st = encode_planes(&maps->egeo, dt, es, rgeo + (size_t)G_NRM * (size_t)ld * es, N, kEdgePlanes, ld);
+  if (st == HW_OK) st = encode_planes(&maps->idx, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, igeo, N, NIGEO, ld);
+  return st;
+}
 
 struct hw_solver {
   hw_options opt;
@@ -247,7 +255,6 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
       cudaMallocHost(&s->h_consv, 4 * sizeof(double)) != cudaSuccess)
     return bail(fail(HW_ECUDA, "stream / pinned host buffer creation failed"));
   // geometry in the solver precision, planes of stride ld
-  const size_t es = precision == HW_FP64 ? 8 : 4;
   const size_t nt = (size_t)M.nt, ld = (size_t)s->ld;
   cudaError_t e;
   if (precision == HW_FP64) {
@@ -269,15 +276,8 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
     e = cudaMemcpyAsync(s->ws + s->L.perm, M.perm.data(), nt * 4, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return bail(fail(HW_ECUDA, std::string("geometry upload: ") + cudaGetErrorString(e)));
   // TMA descriptors of the workspace
-  const CUtensorMapDataType dt = precision == HW_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const int m = s->m;
-  hw_status st = encode_planes(&s->maps.geo, dt, es, s->ws + s->L.rgeo, M.nt, kReconPlanes, s->ld);
-  (void)m;
-  if (st == HW_OK)
-    st = encode_planes(&s->maps.egeo, dt, es, s->ws + s->L.rgeo + (size_t)G_NRM * ld * es, M.nt, kEdgePlanes, s->ld);
-  if (st == HW_OK)
-    st = encode_planes(&s->maps.idx, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, s->ws + s->L.igeo, M.nt, NIGEO, s->ld);
-  if (st != HW_OK) return bail(st);
+  if (hw_status st = hw_encode_plane_maps(&s->maps, precision, s->ws + s->L.rgeo, s->ws + s->L.igeo, M.nt, s->ld))
+    return bail(st);
   prepare_step_kernels(precision, s->eq);
   s->cur = 0;
   if (hw_status st = upload_state(s, Wbar, Vbar, Ybar, 0.0)) return bail(st);

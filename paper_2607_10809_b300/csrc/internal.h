@@ -51,3 +51,11 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
                        HostMesh& M);
 
 }  // namespace hw
+
+// Opaque mesh handle of the C ABI.
+struct hw_mesh {
+  hw::HostMesh M;
+};
+
+// Records the message returned by hw_last_error() on this thread.
+void hw_set_last_error_internal(const char* msg);

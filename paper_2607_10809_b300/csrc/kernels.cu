@@ -118,6 +118,71 @@ __device__ __forceinline__ void tile_range(const TileSet& ts, int N, int tile, i
 
 }  // namespace
 
+// ---------------------------------------------------------------- tile contexts
+// A phase walks the tiles a context exposes.  SingleCtx: one mesh, one time
+// step for all cells.  BatchCtx (several meshes side by side): each tile
+// belongs to one solve, with that solve's time step, buffer parity and status.
+template <typename R> struct SingleCtx {
+  TileSet ts;
+  int N;
+  const R* U;
+  R* Un;
+  double dt;
+  DevScalars* sc;
+  double local_min;   // CFL minimum of this thread over its tiles
+  __device__ __forceinline__ int ntiles() const { return ts.ntiles; }
+  __device__ __forceinline__ bool active(int) const { return true; }
+  __device__ __forceinline__ void range(int tile, int& c0, int& cnt) const { tile_range(ts, N, tile, c0, cnt); }
+  __device__ __forceinline__ const R* uin(int) const { return U; }
+  __device__ __forceinline__ R* uout(int) const { return Un; }
+  __device__ __forceinline__ double dt_of(int) const { return dt; }
+  __device__ __forceinline__ void flag(unsigned f) { atomicOr(&sc->flags, f); }
+  __device__ __forceinline__ void bad_cell(int) { atomicOr(&sc->flags, 1u); }
+  // called by the 32 threads of warp 0 after a tile; v = this thread's value
+  __device__ __forceinline__ void tile_min(int, double v) { local_min = v < local_min ? v : local_min; }
+};
+
+template <typename R> struct BatchCtx {
+  const int4* tiles;   // (first cell, count, solve, 0)
+  int nt;
+  BatchSolve* bs;
+  BatchCtl* ctl;
+  R* U0;
+  R* U1;
+  __device__ __forceinline__ int solve(int tile) const { return tiles[tile].z; }
+  __device__ __forceinline__ int ntiles() const { return nt; }
+  __device__ __forceinline__ bool active(int tile) const {
+    return *(volatile const int*)&bs[solve(tile)].done == 0;
+  }
+  __device__ __forceinline__ void range(int tile, int& c0, int& cnt) const {
+    const int4 e = tiles[tile];
+    c0 = e.x;
+    cnt = e.y;
+  }
+  __device__ __forceinline__ bool odd(int tile) const {
+    return (*(volatile const long long*)&bs[solve(tile)].nsteps) & 1;
+  }
+  __device__ __forceinline__ const R* uin(int tile) const { return odd(tile) ? U1 : U0; }
+  __device__ __forceinline__ R* uout(int tile) const { return odd(tile) ? U0 : U1; }
+  __device__ __forceinline__ double dt_of(int tile) const { return *(volatile const double*)&bs[solve(tile)].dt; }
+  __device__ __forceinline__ void flag(unsigned f) { atomicOr(&ctl->flags, f); }
+  __device__ __forceinline__ void bad_cell(int tile) {
+    atomicOr(&ctl->flags, 1u);
+    atomicExch(&bs[solve(tile)].failed, 1);
+  }
+  __device__ __forceinline__ void tile_min(int tile, double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v < dinf()) atomicMin(&bs[solve(tile)].lam_min_bits, dbits(v));
+  }
+};
+
+// First tile at or after `tile` (stride gridDim.x) that the context keeps.
+template <typename Ctx> __device__ __forceinline__ int next_active(const Ctx& ctx, int tile) {
+  while (tile < ctx.ntiles() && !ctx.active(tile)) tile += gridDim.x;
+  return tile;
+}
+
 // ---------------------------------------------------------------- reconstruction
 template <typename R, int EQ> struct ReconStage {
   static constexpr int m = EqTraits<EQ>::m;
@@ -130,62 +195,60 @@ template <typename R, int EQ> constexpr size_t recon_smem_bytes() {
   return 2 * sizeof(ReconStage<R, EQ>) + sizeof(R) * (EqTraits<EQ>::m + 1) * 6 * kCells + 2 * sizeof(uint64_t) + 128;
 }
 
-template <typename R, int EQ, bool LIM>
-__global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUtensorMap mGeo,
-                                                     const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
-                                                     const R* __restrict__ U, R* __restrict__ Pb, EqParams P,
-                                                     DevScalars* sc, double dt_fixed, TileSet ts) {
+// Shared-memory carve-up common to both phases: stages at the start (128-byte
+// aligned), then phase scratch; the two mbarriers live at a fixed offset set by
+// the caller.
+__device__ __forceinline__ unsigned char* smem_base(unsigned char* raw) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+}
+
+// Reconstruction + Lax-Wendroff over the context's tiles (double-buffered TMA
+// staging).  bar: two initialised mbarriers, ph: their phase bits (kept across
+// calls).  Returns false if a bounded wait gave up (flag 2 raised).
+template <typename R, int EQ, bool LIM, typename Ctx>
+__device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap* mIdx, const EqParams& P,
+                            R* __restrict__ Pb, unsigned char* base, uint64_t* bar, unsigned* ph) {
   constexpr int m = EqTraits<EQ>::m;
   using Stage = ReconStage<R, EQ>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*qs)[6][kCells] = reinterpret_cast<R (*)[6][kCells]>(base + 2 * sizeof(Stage));
   R (*lim)[kCells] = reinterpret_cast<R (*)[kCells]>(base + 2 * sizeof(Stage) + sizeof(R) * m * 6 * kCells);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * (m + 1) * 6 * kCells);
-
-  const volatile DevScalars* vsc = sc;
-  if (vsc->done) return;
-  const R dtr = R(dt_fixed > 0 ? dt_fixed : vsc->dt);   // time nodes of the limiter
-  const int N = G.N, ld = G.ld;
-  const int ntiles = ts.ntiles;
+  const int ntiles = ctx.ntiles();
   const int t = threadIdx.x;
   constexpr unsigned kBytes = sizeof(Stage);
   auto issue = [&](int s, int tile) {
     int c0, cnt;
-    tile_range(ts, N, tile, c0, cnt);
+    ctx.range(tile, c0, cnt);
     mbar_arrive_expect_tx(&bar[s], kBytes);
-    tma_load_2d(&st[s].geo[0][0], &mGeo, c0, 0, &bar[s]);
-    tma_load_2d(&st[s].idx[0][0], &mIdx, c0, 0, &bar[s]);
-    bulk_load(&st[s].u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+    tma_load_2d(&st[s].geo[0][0], mGeo, c0, 0, &bar[s]);
+    tma_load_2d(&st[s].idx[0][0], mIdx, c0, 0, &bar[s]);
+    bulk_load(&st[s].u[0][0], ctx.uin(tile) + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
   };
-  if (t == 0) {
-    prefetch_tensormap(&mGeo); prefetch_tensormap(&mIdx);
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-    if ((int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+  int tile = next_active(ctx, blockIdx.x);
+  if (t == 0 && tile < ntiles) {
+    fence_proxy_async();
+    issue(0, tile);
   }
-  __syncthreads();
-  unsigned phase0 = 0, phase1 = 0;
   int s = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s ^= 1) {
-    const int next = tile + gridDim.x;
+  for (; tile < ntiles; s ^= 1) {
+    const int next = next_active(ctx, tile + gridDim.x);
     if (t == 0 && next < ntiles) {
       fence_proxy_async();
       issue(s ^ 1, next);
     }
-    const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0);
-    if (s) phase1 ^= 1u; else phase0 ^= 1u;
+    const bool ok = mbar_wait(&bar[s], ph[s]);
+    ph[s] ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
-        atomicOr(&sc->flags, 2u);
-        if (next < ntiles) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1);   // drain the copy in flight
+        ctx.flag(2u);
+        if (next < ntiles && mbar_wait(&bar[s ^ 1], ph[s ^ 1])) ph[s ^ 1] ^= 1u;   // drain the copy in flight
       }
-      return;
+      return false;
     }
     int cell0, count;
-    tile_range(ts, N, tile, cell0, count);
+    ctx.range(tile, cell0, count);
+    const R* U = ctx.uin(tile);
+    const R dtr = R(ctx.dt_of(tile));   // time nodes of the limiter
     const Stage& S = st[s];
     if (t < m * kCells) {
       const int lc = t % kCells, c = t / kCells;
@@ -227,76 +290,74 @@ __global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUte
         }
       }
       if constexpr (EQ == kEqEuler && LIM) {
-        {
-          // scale limiter (block-uniform branch): spatial scaling over the six
-          // Gauss points, then the Lax-Wendroff data, then scaling of the
-          // space-time Taylor data over the points and the three time nodes
-          const R gam = R(P.gam);
-          R Wb[4];
+        // scale limiter: spatial scaling over the six Gauss points, then the
+        // Lax-Wendroff data, then scaling of the space-time Taylor data over
+        // the points and the three time nodes
+        const R gam = R(P.gam);
+        R Wb[4];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) Wb[c] = S.u[lc][c];
-          const R pb0 = act ? pressure_of(gam, Wb) : R(0);
-          const bool ok = act && Wb[0] > R(0) && pb0 > R(0);
-          const R eps = ok ? fmin(R(1e-13), fmin(Wb[0], pb0)) : R(0);
-          if (act) lim[qp][lc] = W[0];
-          __syncthreads();
-          R th1 = R(1), th2 = R(1);
-          if (ok) {
-            R rmin = lim[0][lc];
+        for (int c = 0; c < 4; ++c) Wb[c] = S.u[lc][c];
+        const R pb0 = act ? pressure_of(gam, Wb) : R(0);
+        const bool ok = act && Wb[0] > R(0) && pb0 > R(0);
+        const R eps = ok ? fmin(R(1e-13), fmin(Wb[0], pb0)) : R(0);
+        if (act) lim[qp][lc] = W[0];
+        __syncthreads();
+        R th1 = R(1), th2 = R(1);
+        if (ok) {
+          R rmin = lim[0][lc];
 #pragma unroll
-            for (int k = 1; k < 6; ++k) rmin = lim[k][lc] < rmin ? lim[k][lc] : rmin;
-            if (rmin < eps) th1 = (Wb[0] - eps) / (Wb[0] - rmin);
+          for (int k = 1; k < 6; ++k) rmin = lim[k][lc] < rmin ? lim[k][lc] : rmin;
+          if (rmin < eps) th1 = (Wb[0] - eps) / (Wb[0] - rmin);
+        }
+        __syncthreads();
+        R f = R(1);
+        if (ok) {
+          R w[4] = {Wb[0] + th1 * (W[0] - Wb[0]), W[1], W[2], W[3]};
+          if (pressure_of(gam, w) < eps) {
+            R d[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) d[c] = w[c] - Wb[c];
+            f = pressure_root(gam, Wb, d, eps);
           }
-          __syncthreads();
-          R f = R(1);
-          if (ok) {
-            R w[4] = {Wb[0] + th1 * (W[0] - Wb[0]), W[1], W[2], W[3]};
-            if (pressure_of(gam, w) < eps) {
-              R d[4];
+        }
+        if (act) lim[qp][lc] = f;
+        __syncthreads();
+        if (ok) {
 #pragma unroll
-              for (int c = 0; c < 4; ++c) d[c] = w[c] - Wb[c];
-              f = pressure_root(gam, Wb, d, eps);
-            }
+          for (int k = 0; k < 6; ++k) th2 = lim[k][lc] < th2 ? lim[k][lc] : th2;
+        }
+        __syncthreads();
+        if (ok && (th1 != R(1) || th2 != R(1))) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const R th = c == 0 ? th1 * th2 : th2;
+            W[c] = Wb[c] + th * (W[c] - Wb[c]);
+            Wx[c] *= th; Wy[c] *= th; Wxx[c] *= th; Wxy[c] *= th; Wyy[c] *= th;
           }
-          if (act) lim[qp][lc] = f;
-          __syncthreads();
-          if (ok) {
+        }
+        if (act) lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
+        R ft = R(1);
+        if (ok) {
+          const R tau[3] = {R(0), R(0.5) * dtr, dtr};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) th2 = lim[k][lc] < th2 ? lim[k][lc] : th2;
+          for (int si = 0; si < 3; ++si) {
+            R w[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) w[c] = W[c] + Wt[c] * tau[si] + Wtt[c] * (R(0.5) * tau[si] * tau[si]);
+            const R fs = admissible_fraction(gam, Wb, w, eps);
+            ft = fs < ft ? fs : ft;
           }
-          __syncthreads();
-          if (ok && (th1 != R(1) || th2 != R(1))) {
+        }
+        if (act) lim[qp][lc] = ft;
+        __syncthreads();
+        R tht = R(1);
+        if (ok) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const R th = c == 0 ? th1 * th2 : th2;
-              W[c] = Wb[c] + th * (W[c] - Wb[c]);
-              Wx[c] *= th; Wy[c] *= th; Wxx[c] *= th; Wxy[c] *= th; Wyy[c] *= th;
-            }
-          }
-          if (act) lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
-          R ft = R(1);
-          if (ok) {
-            const R tau[3] = {R(0), R(0.5) * dtr, dtr};
+          for (int k = 0; k < 6; ++k) tht = lim[k][lc] < tht ? lim[k][lc] : tht;
+        }
+        if (ok && tht != R(1)) {
 #pragma unroll
-            for (int si = 0; si < 3; ++si) {
-              R w[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) w[c] = W[c] + Wt[c] * tau[si] + Wtt[c] * (R(0.5) * tau[si] * tau[si]);
-              const R fs = admissible_fraction(gam, Wb, w, eps);
-              ft = fs < ft ? fs : ft;
-            }
-          }
-          if (act) lim[qp][lc] = ft;
-          __syncthreads();
-          R tht = R(1);
-          if (ok) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) tht = lim[k][lc] < tht ? lim[k][lc] : tht;
-          }
-          if (ok && tht != R(1)) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) { W[c] = Wb[c] + tht * (W[c] - Wb[c]); Wt[c] *= tht; Wtt[c] *= tht; }
-          }
+          for (int c = 0; c < 4; ++c) { W[c] = Wb[c] + tht * (W[c] - Wb[c]); Wt[c] *= tht; Wtt[c] *= tht; }
         }
       } else if (act) {
         lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
@@ -309,7 +370,9 @@ __global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUte
       }
     }
     __syncthreads();
+    tile = next;
   }
+  return true;
 }
 
 // ---------------------------------------------------------------- flux + update
@@ -326,75 +389,55 @@ template <typename R, int EQ> constexpr size_t edge_smem_bytes() {
          sizeof(R) * EqTraits<EQ>::m * kCells + 2 * sizeof(uint64_t) + 128;
 }
 
-template <typename R, int EQ>
-__global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUtensorMap mEgeo,
-                                                    const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
-                                                    const R* __restrict__ U, R* __restrict__ Un,
-                                                    const R* __restrict__ Pb, EqParams P, DevScalars* sc,
-                                                    double dt_fixed, TileSet ts) {
+// Flux at the Gauss-Lobatto time nodes, cell-average and Green-Gauss update,
+// CFL candidates over the context's tiles.  Returns false if a bounded wait
+// gave up.
+template <typename R, int EQ, typename Ctx>
+__device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap* mIdx, const EqParams& P,
+                           const R* __restrict__ Pb, unsigned char* base, uint64_t* bar, unsigned* ph) {
   constexpr int m = EqTraits<EQ>::m;
   using Stage = EdgeStage<R, EQ>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*part)[m][6][kCells] = reinterpret_cast<R (*)[m][6][kCells]>(base + 2 * sizeof(Stage));
   R (*wn)[kCells] = reinterpret_cast<R (*)[kCells]>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells);
-  uint64_t* bar =
-      reinterpret_cast<uint64_t*>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells + sizeof(R) * m * kCells);
-
-  const int N = G.N, ld = G.ld;
-  const int ntiles = ts.ntiles;
+  const int ntiles = ctx.ntiles();
   const int t = threadIdx.x;
-  const volatile DevScalars* vs = sc;
-  if (vs->done) {  // target reached: keep the state, preserving the buffer alternation
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      int cell0, count;
-      tile_range(ts, N, tile, cell0, count);
-      for (int k = t; k < 3 * m * count; k += kThreads) Un[(size_t)cell0 * 3 * m + k] = U[(size_t)cell0 * 3 * m + k];
-    }
-    return;
-  }
-  const double dt = dt_fixed > 0 ? dt_fixed : vs->dt;
-  const R dtr = R(dt);
   constexpr unsigned kBytes = sizeof(Stage);
   auto issue = [&](int s, int tile) {
     int c0, cnt;
-    tile_range(ts, N, tile, c0, cnt);
+    ctx.range(tile, c0, cnt);
     mbar_arrive_expect_tx(&bar[s], kBytes);
-    tma_load_2d(&st[s].geo[0][0], &mEgeo, c0, 0, &bar[s]);
-    tma_load_2d(&st[s].idx[0][0], &mIdx, c0, 0, &bar[s]);
+    tma_load_2d(&st[s].geo[0][0], mEgeo, c0, 0, &bar[s]);
+    tma_load_2d(&st[s].idx[0][0], mIdx, c0, 0, &bar[s]);
     bulk_load(&st[s].pb[0][0], Pb + (size_t)c0 * 18 * m, kCells * 18 * m * sizeof(R), &bar[s]);
-    bulk_load(&st[s].u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+    bulk_load(&st[s].u[0][0], ctx.uin(tile) + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
   };
-  if (t == 0) {
-    prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-    if ((int)blockIdx.x < ntiles) issue(0, blockIdx.x);
+  int tile = next_active(ctx, blockIdx.x);
+  if (t == 0 && tile < ntiles) {
+    fence_proxy_async();
+    issue(0, tile);
   }
-  __syncthreads();
-  double local_min = dinf();
-  unsigned phase0 = 0, phase1 = 0;
   int s = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s ^= 1) {
-    const int next = tile + gridDim.x;
+  for (; tile < ntiles; s ^= 1) {
+    const int next = next_active(ctx, tile + gridDim.x);
     if (t == 0 && next < ntiles) {
       fence_proxy_async();
       issue(s ^ 1, next);
     }
-    const bool ok = mbar_wait(&bar[s], s ? phase1 : phase0);
-    if (s) phase1 ^= 1u; else phase0 ^= 1u;
+    const bool ok = mbar_wait(&bar[s], ph[s]);
+    ph[s] ^= 1u;
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
-        atomicOr(&sc->flags, 2u);
-        if (next < ntiles) mbar_wait(&bar[s ^ 1], s ? phase0 : phase1);
+        ctx.flag(2u);
+        if (next < ntiles && mbar_wait(&bar[s ^ 1], ph[s ^ 1])) ph[s ^ 1] ^= 1u;
       }
-      local_min = dinf();
-      break;
+      return false;
     }
     int cell0, count;
-    tile_range(ts, N, tile, cell0, count);
+    ctx.range(tile, cell0, count);
+    const R* U = ctx.uin(tile);
+    R* Un = ctx.uout(tile);
+    const R dtr = R(ctx.dt_of(tile));
     const Stage& S = st[s];
     {
       const int lc = t % kCells, qp = t / kCells, i = cell0 + lc;
@@ -481,20 +524,187 @@ __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUten
       }
     }
     __syncthreads();
-    if (t < count) {
-      R Wnew[m];
+    if (t < kCells) {
+      double v = dinf();
+      if (t < count) {
+        R Wnew[m];
 #pragma unroll
-      for (int c = 0; c < m; ++c) Wnew[c] = wn[c][t];
-      if (!physical<R, EQ>(Wnew, P)) atomicOr(&sc->flags, 1u);
-      const R lam = spectral_radius_all<R, EQ>(Wnew, P);
-      if (lam > R(0)) {
-        const double v = (double)(S.geo[G_INR - G_NRM][t] / lam);
-        if (v >= 0 && v < local_min) local_min = v;
+        for (int c = 0; c < m; ++c) Wnew[c] = wn[c][t];
+        if (!physical<R, EQ>(Wnew, P)) ctx.bad_cell(tile);
+        const R lam = spectral_radius_all<R, EQ>(Wnew, P);
+        if (lam > R(0)) {
+          const double r = (double)(S.geo[G_INR - G_NRM][t] / lam);
+          if (r >= 0) v = r;
+        }
       }
+      ctx.tile_min(tile, v);
     }
     __syncthreads();
+    tile = next;
   }
-  finish_step(sc, local_min, dt, true);
+  return true;
+}
+
+// ---------------------------------------------------------------- single-solve kernels
+template <typename R, int EQ, bool LIM>
+__global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUtensorMap mGeo,
+                                                     const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
+                                                     const R* __restrict__ U, R* __restrict__ Pb, EqParams P,
+                                                     DevScalars* sc, double dt_fixed, TileSet ts) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + recon_smem_bytes<R, EQ>() - 128 - 2 * sizeof(uint64_t));
+  const volatile DevScalars* vsc = sc;
+  if (vsc->done) return;
+  SingleCtx<R> ctx{ts, G.N, U, nullptr, dt_fixed > 0 ? dt_fixed : vsc->dt, sc, dinf()};
+  if (threadIdx.x == 0) {
+    prefetch_tensormap(&mGeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph[2] = {0u, 0u};
+  recon_phase<R, EQ, LIM>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
+}
+
+template <typename R, int EQ>
+__global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUtensorMap mEgeo,
+                                                    const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
+                                                    const R* __restrict__ U, R* __restrict__ Un,
+                                                    const R* __restrict__ Pb, EqParams P, DevScalars* sc,
+                                                    double dt_fixed, TileSet ts) {
+  constexpr int m = EqTraits<EQ>::m;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + edge_smem_bytes<R, EQ>() - 128 - 2 * sizeof(uint64_t));
+  const int N = G.N;
+  const int t = threadIdx.x;
+  const volatile DevScalars* vs = sc;
+  if (vs->done) {  // target reached: keep the state, preserving the buffer alternation
+    for (int tile = blockIdx.x; tile < ts.ntiles; tile += gridDim.x) {
+      int cell0, count;
+      tile_range(ts, N, tile, cell0, count);
+      for (int k = t; k < 3 * m * count; k += kThreads) Un[(size_t)cell0 * 3 * m + k] = U[(size_t)cell0 * 3 * m + k];
+    }
+    return;
+  }
+  const double dt = dt_fixed > 0 ? dt_fixed : vs->dt;
+  SingleCtx<R> ctx{ts, N, U, Un, dt, sc, dinf()};
+  if (t == 0) {
+    prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph[2] = {0u, 0u};
+  if (!edge_phase<R, EQ>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph)) ctx.local_min = dinf();
+  finish_step(sc, ctx.local_min, dt, true);
+}
+
+// ---------------------------------------------------------------- batched persistent kernel
+// Grid-wide barrier of a cooperative launch; the spin is bounded: on time-out
+// the barrier reports false (flag 2 raised by the caller).  `skip` (tests
+// only) makes this block leave without arriving, so that the others time out.
+__device__ bool grid_barrier(BatchCtl* ctl, unsigned long long spin_limit, bool skip) {
+  __shared__ int ok_s;
+  // the phase's plain stores (edge-point data, new states) are read by bulk
+  // copies after the barrier: order them for the async proxy first
+  fence_proxy_async_global();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (skip) {
+      ok = 0;
+    } else {
+      volatile unsigned* gen = &ctl->bar_gen;
+      const unsigned g = *gen;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(&ctl->bar_count, 0u);
+        __threadfence();
+        atomicAdd(&ctl->bar_gen, 1u);
+      } else {
+        unsigned long long it = 0;
+        while (*gen == g) {
+          if (++it > spin_limit) { ok = 0; break; }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// All steps of all solves of a batch in one launch: per step a
+// reconstruction phase over the tiles of the running solves, a grid barrier,
+// the flux/update phase (per-solve CFL minima), a barrier, the per-solve time
+// step / status update, a barrier.  Leaves when no solve is running or after
+// max_steps steps.
+template <typename R, int EQ, bool LIM>
+__global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUtensorMap mGeo,
+                                                     const __grid_constant__ CUtensorMap mEgeo,
+                                                     const __grid_constant__ CUtensorMap mIdx, R* U0, R* U1,
+                                                     R* __restrict__ Pb, EqParams P, BatchCtx<R> ctx, int nsolves,
+                                                     double cfl, int max_steps, unsigned long long spin_limit,
+                                                     int withhold_block) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  constexpr size_t kStageBytes = recon_smem_bytes<R, EQ>() > edge_smem_bytes<R, EQ>() ? recon_smem_bytes<R, EQ>()
+                                                                                     : edge_smem_bytes<R, EQ>();
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + kStageBytes - 128 - 2 * sizeof(uint64_t));
+  BatchCtl* ctl = ctx.ctl;
+  if (threadIdx.x == 0) {
+    prefetch_tensormap(&mGeo); prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph[2] = {0u, 0u};
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool skip = (int)blockIdx.x == withhold_block;
+  bool ok = true;
+  for (int step = 0; step < max_steps && ok; ++step) {
+    const int slot = step & 1;
+    ok = recon_phase<R, EQ, LIM>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
+    if (!grid_barrier(ctl, spin_limit, skip || !ok)) ok = false;
+    if (!ok) break;
+    ok = edge_phase<R, EQ>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph);
+    if (!grid_barrier(ctl, spin_limit, !ok)) ok = false;
+    if (!ok) break;
+    // per-solve step, status and next time step (one thread per solve)
+    if (gid < nsolves) {
+      volatile BatchSolve* b = &ctx.bs[gid];
+      if (!b->done) {
+        const double tn = b->t + b->dt;
+        b->t = tn;
+        b->nsteps = b->nsteps + 1;
+        const double mn = __longlong_as_double((long long)atomicAdd(&ctx.bs[gid].lam_min_bits, 0ull));
+        double dtn = cfl * mn;
+        int done = 0;
+        if (b->failed) done = 1;
+        else if (tn >= b->T * (1.0 - 1e-14)) done = 1;
+        else if (tn + dtn > b->T) dtn = b->T - tn;
+        b->dt = dtn;
+        b->done = done;
+        atomicExch(&ctx.bs[gid].lam_min_bits, dbits(dinf()));
+        if (!done) atomicAdd(&ctl->active[slot], 1u);
+      }
+    }
+    if (gid == 0) {
+      atomicExch(&ctl->active[slot ^ 1], 0u);
+      atomicAdd(&ctl->steps_run, 1);
+    }
+    if (!grid_barrier(ctl, spin_limit, false)) { ok = false; break; }
+    if (*(volatile unsigned*)&ctl->active[slot] == 0) break;
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(&ctl->flags, 2u);
 }
 
 // CFL step of the current state (after an upload or a change of target).
@@ -581,6 +791,62 @@ __global__ void k_set_target(DevScalars* sc, double T, int has_T) {
       else if (sc->t + sc->dt > T) sc->dt = T - sc->t;
     }
     sc->done = done;
+  }
+}
+
+// ---------------------------------------------------------------- batch helpers
+// CFL candidates of every tile of a batch (state buffer 0 at set-up): warp
+// minimum, one atomic per tile on the tile's solve.
+template <typename R, int EQ>
+__global__ void __launch_bounds__(256) k_batch_cfl(GeoView<R> G, const R* __restrict__ U, const int4* __restrict__ tiles,
+                                                   int ntiles, EqParams P, BatchSolve* bs, BatchCtl* ctl) {
+  constexpr int m = EqTraits<EQ>::m;
+  const int tile = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x & 31;
+  if (tile >= ntiles) return;   // whole warps leave together
+  const int4 e = tiles[tile];
+  double v = dinf();
+  if (lane < e.y) {
+    const int i = e.x + lane;
+    R W[m];
+#pragma unroll
+    for (int c = 0; c < m; ++c) W[c] = U[(size_t)i * 3 * m + c];
+    if (!physical<R, EQ>(W, P)) {
+      atomicOr(&ctl->flags, 1u);
+      atomicExch(&bs[e.z].failed, 1);
+    }
+    const R lam = spectral_radius_all<R, EQ>(W, P);
+    if (lam > R(0)) {
+      const double r = (double)(G.r(G_INR, i) / lam);
+      if (r >= 0) v = r;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0 && v < dinf()) atomicMin(&bs[e.z].lam_min_bits, dbits(v));
+}
+
+// Per solve: time step from the CFL minimum (clipped to the target when one is
+// set), done flag; resets the minimum.
+__global__ void k_batch_dt(BatchSolve* bs, int n, double cfl, double T, int has_T) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  BatchSolve& b = bs[s];
+  const double mn = __longlong_as_double((long long)b.lam_min_bits);
+  if (has_T) b.T = T;
+  if (mn < dinf()) b.dt = cfl * mn;
+  b.lam_min_bits = dbits(dinf());
+  int done = b.failed ? 1 : 0;
+  if (has_T) {
+    if (b.t >= b.T * (1.0 - 1e-14)) done = 1;
+    else if (b.t + b.dt > b.T) b.dt = b.T - b.t;
+  }
+  b.done = done;
+}
+
+__global__ void k_batch_reset_ctl(BatchCtl* ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctl->bar_count = 0u; ctl->bar_gen = 0u; ctl->active[0] = 0u; ctl->active[1] = 0u; ctl->flags = 0u;
+    ctl->steps_run = 0;
   }
 }
 
@@ -689,6 +955,75 @@ void launch_scatter(int prec, const double* host_order, const int32_t* perm, int
   else
     k_scatter_state<float><<<nb, 256, 0, st>>>(host_order, perm, N, ld, planes, reinterpret_cast<float*>(U));
 }
+
+namespace {
+template <typename R, int EQ, bool LIM> constexpr size_t batch_smem() {
+  return recon_smem_bytes<R, EQ>() > edge_smem_bytes<R, EQ>() ? recon_smem_bytes<R, EQ>() : edge_smem_bytes<R, EQ>();
+}
+template <typename R, int EQ, bool LIM> int batch_cap_t() {
+  static const int cap = [] {
+    int per_sm = 0;
+    cudaFuncSetAttribute(k_batch<R, EQ, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<R, EQ, LIM>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<R, EQ, LIM>, kThreads, batch_smem<R, EQ, LIM>());
+    return per_sm;
+  }();
+  return cap;
+}
+template <typename R, int EQ, bool LIM> cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t st) {
+  BatchCtx<R> ctx{a.tiles, a.ntiles, a.bs, a.ctl, reinterpret_cast<R*>(a.U0), reinterpret_cast<R*>(a.U1)};
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(a.grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = batch_smem<R, EQ, LIM>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch<R, EQ, LIM>, a.maps->geo, a.maps->egeo, a.maps->idx,
+                            reinterpret_cast<R*>(a.U0), reinterpret_cast<R*>(a.U1), reinterpret_cast<R*>(a.Pb), a.P,
+                            ctx, a.nsolves, a.cfl, a.max_steps, a.spin_limit, a.withhold_block);
+}
+template <typename R, int EQ> void launch_batch_cfl_t(const BatchArgs& a, cudaStream_t st) {
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
+  k_batch_cfl<R, EQ><<<(a.ntiles * 32 + 255) / 256, 256, 0, st>>>(G, reinterpret_cast<const R*>(a.U0), a.tiles,
+                                                                  a.ntiles, a.P, a.bs, a.ctl);
+}
+}  // namespace
+
+int batch_blocks_per_sm(int prec, int eq, bool lim) {
+  if (prec == 0) {
+    if (eq == 0) return batch_cap_t<double, 0, false>();
+    if (eq == 1) return batch_cap_t<double, 1, false>();
+    return lim ? batch_cap_t<double, 2, true>() : batch_cap_t<double, 2, false>();
+  }
+  if (eq == 0) return batch_cap_t<float, 0, false>();
+  if (eq == 1) return batch_cap_t<float, 1, false>();
+  return lim ? batch_cap_t<float, 2, true>() : batch_cap_t<float, 2, false>();
+}
+
+cudaError_t launch_batch(int prec, int eq, const BatchArgs& a, cudaStream_t st) {
+  const bool lim = eq == 2 && a.P.positivity;
+  if (prec == 0) {
+    if (eq == 0) return launch_batch_t<double, 0, false>(a, st);
+    if (eq == 1) return launch_batch_t<double, 1, false>(a, st);
+    return lim ? launch_batch_t<double, 2, true>(a, st) : launch_batch_t<double, 2, false>(a, st);
+  }
+  if (eq == 0) return launch_batch_t<float, 0, false>(a, st);
+  if (eq == 1) return launch_batch_t<float, 1, false>(a, st);
+  return lim ? launch_batch_t<float, 2, true>(a, st) : launch_batch_t<float, 2, false>(a, st);
+}
+
+void launch_batch_cfl(int prec, int eq, const BatchArgs& a, cudaStream_t st) {
+  HW_DISPATCH(launch_batch_cfl_t, prec, eq, a, st);
+}
+
+void launch_batch_dt(BatchSolve* bs, int n, double cfl, double T, int has_T, cudaStream_t st) {
+  k_batch_dt<<<(n + 127) / 128, 128, 0, st>>>(bs, n, cfl, T, has_T);
+}
+
+void launch_batch_reset_ctl(BatchCtl* ctl, cudaStream_t st) { k_batch_reset_ctl<<<1, 32, 0, st>>>(ctl); }
 
 void launch_gather(int prec, const void* U, const int32_t* perm, int N, int ld, int planes, double* host_order,
                    cudaStream_t st) {

@@ -33,6 +33,26 @@ struct TensorMaps {
   CUtensorMap idx;      // neighbour planes + packed edge indices, box kCells x 4
 };
 
+// Per-solve device state of a batch.
+struct BatchSolve {
+  double t;                          // time
+  double dt;                         // next step
+  double T;                          // target time
+  unsigned long long lam_min_bits;   // CFL minimum of the running step (bits of a positive double)
+  long long nsteps;                  // steps taken (its parity selects the state buffer)
+  int done;                          // target reached or failed
+  int failed;                        // state became non-finite / non-physical
+};
+
+// Control block of a batched launch (grid barrier, running-solve counts, flags).
+struct BatchCtl {
+  unsigned bar_count;
+  unsigned bar_gen;
+  unsigned active[2];
+  unsigned flags;                    // bit 0: non-physical state, bit 1: a bounded wait gave up
+  int steps_run;
+};
+
 struct StepArgs {
   const void* rgeo;        // [NRGEO][ld] in the solver precision
   const int32_t* igeo;     // [NIGEO][ld]
@@ -48,6 +68,36 @@ struct StepArgs {
   double dt_fixed;         // > 0: use this step instead of the device CFL step
   EqParams P;
 };
+
+// Arguments of the batched persistent kernel.
+struct BatchArgs {
+  const void* rgeo;
+  const int32_t* igeo;
+  int N;                    // cells of all solves (with padding between solves)
+  int ld;
+  void* U0;                 // state buffer 0 [ld][3m]
+  void* U1;                 // state buffer 1
+  void* Pb;                 // edge-point buffer [ld][6][3][m]
+  const TensorMaps* maps;
+  const int4* tiles;        // (first cell, count, solve, 0)
+  int ntiles;
+  BatchSolve* bs;
+  BatchCtl* ctl;
+  int nsolves;
+  double cfl;
+  int max_steps;            // steps per launch
+  unsigned long long spin_limit;
+  int withhold_block;       // tests: this block skips its first barrier arrival (-1: none)
+  int grid;
+  EqParams P;
+};
+
+// Resident blocks per SM of the batched kernel (cooperative launch limit).
+int batch_blocks_per_sm(int prec, int eq, bool lim);
+cudaError_t launch_batch(int prec, int eq, const BatchArgs& a, cudaStream_t st);
+void launch_batch_cfl(int prec, int eq, const BatchArgs& a, cudaStream_t st);
+void launch_batch_dt(BatchSolve* bs, int n, double cfl, double T, int has_T, cudaStream_t st);
+void launch_batch_reset_ctl(BatchCtl* ctl, cudaStream_t st);
 
 // Sets the kernels' shared-memory limits and caches their resident-block
 // counts; call once per (precision, equation) before any stream capture.
@@ -66,3 +116,7 @@ void launch_gather(int prec, const void* U, const int32_t* perm, int N, int ld, 
                    cudaStream_t st);
 
 }  // namespace hw
+
+#include "../../include/hweno.h"
+// TMA descriptors of the geometry and index planes of a workspace.
+hw_status hw_encode_plane_maps(hw::TensorMaps* maps, int precision, char* rgeo, char* igeo, int64_t N, int64_t ld);

@@ -25,7 +25,10 @@ PRECISIONS = {"fp64": 0, "fp32": 1}
 EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_ntri", "hw_mesh_neighbors",
             "hw_mesh_permutation", "hw_workspace_bytes", "hw_state_init", "hw_set_state", "hw_step", "hw_run_to",
             "hw_get_state", "hw_conservation", "hw_status_flags", "hw_time", "hw_profile", "hw_profile_read",
-            "hw_solver_destroy", "hw_last_error", "hw_step_static_scratch"]
+            "hw_solver_destroy", "hw_last_error", "hw_step_static_scratch", "hw_batch_schedule_default",
+            "hw_batch_workspace_bytes", "hw_batch_create", "hw_batch_set_schedule", "hw_batch_get_schedule",
+            "hw_batch_autotune", "hw_batch_run_to", "hw_batch_steps", "hw_batch_reset", "hw_batch_get_state",
+            "hw_batch_destroy"]
 
 
 class HwError(RuntimeError):
@@ -38,6 +41,15 @@ class Options(ctypes.Structure):
     _fields_ = [("eq", ctypes.c_int32), ("positivity", ctypes.c_int32), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("gamma_gas", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("gamma_lin", ctypes.c_double * 4), ("eps", ctypes.c_double)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("tile_order", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32), ("withhold_block", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _lib = None
@@ -74,6 +86,17 @@ def load():
         "hw_solver_destroy": (ctypes.c_int, [vp]),
         "hw_last_error": (ctypes.c_char_p, []),
         "hw_step_static_scratch": (ctypes.c_int, [vp, d]),
+        "hw_batch_schedule_default": (None, [P(Schedule)]),
+        "hw_batch_workspace_bytes": (ctypes.c_int, [vp, i32, P(Options), i32, P(sz)]),
+        "hw_batch_create": (ctypes.c_int, [vp, i32, P(Options), i32, vp, vp, vp, vp, sz, vp, P(vp)]),
+        "hw_batch_set_schedule": (ctypes.c_int, [vp, P(Schedule)]),
+        "hw_batch_get_schedule": (ctypes.c_int, [vp, P(Schedule), P(i32)]),
+        "hw_batch_autotune": (ctypes.c_int, [vp, i32, P(Schedule), P(d)]),
+        "hw_batch_run_to": (ctypes.c_int, [vp, d, P(i64)]),
+        "hw_batch_steps": (ctypes.c_int, [vp, i32, P(d)]),
+        "hw_batch_reset": (ctypes.c_int, [vp]),
+        "hw_batch_get_state": (ctypes.c_int, [vp, i32, vp, vp, vp, P(d), P(i64), P(i32)]),
+        "hw_batch_destroy": (ctypes.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -234,3 +257,83 @@ class Solver:
 
     def __del__(self):
         self.close()
+
+
+class Batch:
+    """Many independent solves advanced together in one persistent launch
+    (hw_batch).  meshes: list of inputs.Mesh; states: list of U[3, m, nt]."""
+
+    def __init__(self, meshes, states, eq="euler", precision="fp32", stream=None, **opt_kw):
+        import torch
+        self.meshes = [m if isinstance(m, Mesh) else Mesh(m) for m in meshes]
+        self.n = len(self.meshes)
+        self.m = 4 if eq == "euler" else 1
+        self.opt = options(eq, **opt_kw)
+        self.precision = precision
+        hs = (ctypes.c_void_p * self.n)(*[mm.h.value for mm in self.meshes])
+        self._hs = hs
+        n = ctypes.c_size_t()
+        _check(load().hw_batch_workspace_bytes(hs, self.n, ctypes.byref(self.opt), PRECISIONS[precision],
+                                               ctypes.byref(n)))
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._states = [np.ascontiguousarray(U, dtype=np.float64) for U in states]
+        for U, mm in zip(self._states, self.meshes):
+            assert U.shape == (3, self.m, mm.nt), U.shape
+        W = (ctypes.c_void_p * self.n)(*[U[0].ctypes.data for U in self._states])
+        V = (ctypes.c_void_p * self.n)(*[U[1].ctypes.data for U in self._states])
+        Y = (ctypes.c_void_p * self.n)(*[U[2].ctypes.data for U in self._states])
+        h = ctypes.c_void_p()
+        _check(load().hw_batch_create(hs, self.n, ctypes.byref(self.opt), PRECISIONS[precision], W, V, Y,
+                                      ctypes.c_void_p(self.workspace.data_ptr()), n.value,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def schedule(self):
+        s = Schedule(); g = ctypes.c_int32()
+        _check(load().hw_batch_get_schedule(self.h, ctypes.byref(s), ctypes.byref(g)))
+        d = s.as_dict(); d["grid_blocks"] = g.value
+        return d
+
+    def set_schedule(self, **kw):
+        s = Schedule(); g = ctypes.c_int32()
+        _check(load().hw_batch_get_schedule(self.h, ctypes.byref(s), ctypes.byref(g)))
+        for k, v in kw.items():
+            setattr(s, k, v)
+        _check(load().hw_batch_set_schedule(self.h, ctypes.byref(s)))
+
+    def autotune(self, trial_steps=8):
+        s = Schedule(); ms = ctypes.c_double()
+        _check(load().hw_batch_autotune(self.h, int(trial_steps), ctypes.byref(s), ctypes.byref(ms)))
+        d = s.as_dict(); d["trial_ms"] = ms.value
+        return d
+
+    def run_to(self, T):
+        cs = ctypes.c_int64()
+        _check(load().hw_batch_run_to(self.h, float(T), ctypes.byref(cs)))
+        return cs.value
+
+    def steps(self, k):
+        ms = ctypes.c_double()
+        _check(load().hw_batch_steps(self.h, int(k), ctypes.byref(ms)))
+        return ms.value
+
+    def reset(self):
+        _check(load().hw_batch_reset(self.h))
+
+    def get_state(self, k):
+        U = np.empty((3, self.m, self.meshes[k].nt))
+        t = ctypes.c_double(); ns = ctypes.c_int64(); f = ctypes.c_int32()
+        _check(load().hw_batch_get_state(self.h, int(k), U[0].ctypes.data_as(ctypes.c_void_p),
+                                         U[1].ctypes.data_as(ctypes.c_void_p), U[2].ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(t), ctypes.byref(ns), ctypes.byref(f)))
+        return U, t.value, ns.value, bool(f.value)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.hw_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
