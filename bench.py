@@ -287,12 +287,61 @@ def run_ours(args, rank, world, local_rank):
                  "clocks": r64["clocks"]},
         "status_flags": {"fp32": r32["flags"], "fp64": r64["flags"]},
     }
+    if not args.no_batch:
+        line["batched"] = batched_leg(args, world)
     if not args.no_cpu:
-        import multiprocessing as mp  # noqa: F401  (oracle runs in this process, single thread)
         rate, n, el = cpu_oracle_rate(mesh, U0, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"one FP64 oracle step over a patch of {n} of {N} cells ({el:.1f} s)"}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- batched leg
+def batched_leg(args, world):
+    """256 four-quadrant Riemann solves (2k-40k triangles each, FP32, scale
+    limiter) advanced to T = 0.25 in one persistent launch with the autotuned
+    schedule, against the same solves run one after another through the
+    single-solve path."""
+    import torch
+    from paper_2607_10809_b300 import hweno
+    meshes, states = I.config4_batch(args.batch_solves)
+    T = 0.25
+    b = hweno.Batch(meshes, states, eq="euler", precision="fp32", positivity=True)
+    best = b.autotune(trial_steps=6)
+    b.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    try:
+        cell_steps = b.run_to(T)
+        status = "ok"
+    except hweno.HwError as e:
+        status = str(e).split(":")[0]
+        cell_steps = sum(b.get_state(k)[2] * m.nt for k, m in enumerate(meshes))
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    failed = sum(1 for k in range(len(meshes)) if b.get_state(k)[3])
+    steps = [b.get_state(k)[2] for k in range(len(meshes))]
+    b.close()
+    # the same solves one by one through the single-solve path (graph-captured run_to)
+    seq_cells, seq_time = 0, 0.0
+    for mesh, U0 in zip(meshes, states):
+        s = hweno.Solver(mesh, U0, eq="euler", precision="fp32", positivity=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        try:
+            n = s.run_to(T)
+        except hweno.HwError:
+            n = s.time()[2]
+        torch.cuda.synchronize()
+        seq_time += time.perf_counter() - t1
+        seq_cells += n * mesh.nt
+        s.close()
+    return {"workload": f"{len(meshes)} four-quadrant Riemann solves on [0,1]^2, "
+                        f"{sum(m.nt for m in meshes)} triangles, FP32 + scale limiter, T=0.25",
+            "value": cell_steps / el, "unit": UNIT, "seconds": el, "cell_steps": int(cell_steps),
+            "steps_min_max": [int(min(steps)), int(max(steps))], "failed_solves": failed, "status": status,
+            "schedule": best, "single_solve_sequential_value": seq_cells / seq_time,
+            "single_solve_sequential_seconds": seq_time}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -338,6 +387,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (many solves) leg")
+    ap.add_argument("--batch-solves", type=int, default=256)
     ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64"], help="precisions to run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-cells", type=int, default=4000)

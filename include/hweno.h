@@ -168,6 +168,33 @@ hw_status hw_solver_destroy(hw_solver* s);
 hw_status hw_step_static_scratch(hw_solver* s, double dt);
 
 /* ---------------------------------------------------------------------------
+ * Device-side state buffers and the adjoint of a step.
+ * An internal state buffer holds the state of every cell in the library's
+ * internal order and precision: hw_state_bytes() bytes, caller-allocated
+ * device memory, 16-byte aligned. */
+hw_status hw_state_bytes(const hw_solver* s, size_t* bytes);
+/* Copy the current state to / from an internal buffer (device to device,
+ * asynchronous on the stream).  Import also sets the time to t and recomputes
+ * the CFL step. */
+hw_status hw_state_export(hw_solver* s, void* dst);
+hw_status hw_state_import(hw_solver* s, const void* src, double t);
+/* Convert host arrays (caller numbering, double, as for hw_get_state) to an
+ * internal buffer and back; pure permutation and precision conversion (used
+ * for cotangents); synchronise. */
+hw_status hw_host_to_internal(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, void* dst);
+hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, double* Vbar, double* Ybar);
+/* Adjoint (vector-Jacobian product) of one step of size dt held fixed:
+ * Ubar_n = (dU^{n+1}/dU^n)^T Ubar_next, for the Euler equations without the
+ * scale limiter.  U_n, Ubar_next, Ubar_n: internal buffers (device); the
+ * forward Taylor data of U_n are recomputed.  Non-smooth points (|.| in the
+ * nonlinear weights and the viscosity, max in the viscosity) follow the
+ * branch of the forward evaluation.  scratch: device memory of
+ * hw_adjoint_scratch_bytes(), 256-byte aligned.  Asynchronous on the stream. */
+hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes);
+hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Ubar_next, void* Ubar_n, void* scratch,
+                          size_t scratch_bytes);
+
+/* ---------------------------------------------------------------------------
  * Batched runs: many independent solves (same options, meshes of any sizes)
  * advanced together.  All time steps of all solves run inside one persistent
  * cooperative kernel launch (captured in a CUDA graph): per step a

@@ -500,3 +500,120 @@ extern "C" hw_status hw_step_static_scratch(hw_solver* s, double dt) {
   s->cur = 1 - s->cur;
   return HW_OK;
 }
+
+// ---------------------------------------------------------------------------
+// State buffers on the device, and the adjoint of a step.
+namespace {
+size_t state_bytes(const hw_solver* s) { return (size_t)3 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4); }
+
+struct AdjointScratch {
+  size_t Pbb, Ubw, Cb, sc, total;
+};
+AdjointScratch adjoint_layout(const hw_solver* s) {
+  const size_t es = s->prec == HW_FP64 ? 8 : 4, ld = (size_t)s->ld, m = (size_t)s->m;
+  AdjointScratch a{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  a.Pbb = take(18 * m * ld * es);
+  a.Ubw = take(3 * m * ld * es);
+  a.Cb = take(12 * m * ld * es);
+  a.sc = take(sizeof(DevScalars));
+  a.total = o;
+  return a;
+}
+}  // namespace
+
+extern "C" {
+
+hw_status hw_state_bytes(const hw_solver* s, size_t* bytes) {
+  if (!s || !bytes) return fail(HW_EINVAL, "null pointer");
+  *bytes = state_bytes(s);
+  return HW_OK;
+}
+
+hw_status hw_state_export(hw_solver* s, void* dst) {
+  if (!s || !dst) return fail(HW_EINVAL, "null pointer");
+  HW_CUDA(cudaMemcpyAsync(dst, s->U(s->cur), state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+  return HW_OK;
+}
+
+hw_status hw_state_import(hw_solver* s, const void* src, double t) {
+  if (!s || !src) return fail(HW_EINVAL, "null pointer");
+  HW_CUDA(cudaMemcpyAsync(s->U(s->cur), src, state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+  launch_reset(s->sc(), t, s->opt.cfl, s->stream);
+  launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
+  HW_CUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+hw_status hw_host_to_internal(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, void* dst) {
+  if (!s || !Wbar || !Vbar || !Ybar || !dst) return fail(HW_EINVAL, "null pointer");
+  const size_t plane = (size_t)s->m * s->N * sizeof(double);
+  double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
+  HW_CUDA(cudaMemcpyAsync(stage, Wbar, plane, cudaMemcpyHostToDevice, s->stream));
+  HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + plane, Vbar, plane, cudaMemcpyHostToDevice, s->stream));
+  HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + 2 * plane, Ybar, plane, cudaMemcpyHostToDevice, s->stream));
+  launch_scatter(s->prec, stage, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld,
+                 3 * s->m, dst, s->stream);
+  HW_CUDA(cudaGetLastError());
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  return HW_OK;
+}
+
+hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, double* Vbar, double* Ybar) {
+  if (!s || !src) return fail(HW_EINVAL, "null pointer");
+  const size_t plane = (size_t)s->m * s->N * sizeof(double);
+  double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
+  launch_gather(s->prec, src, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld, 3 * s->m,
+                stage, s->stream);
+  HW_CUDA(cudaGetLastError());
+  if (Wbar) HW_CUDA(cudaMemcpyAsync(Wbar, stage, plane, cudaMemcpyDeviceToHost, s->stream));
+  if (Vbar) HW_CUDA(cudaMemcpyAsync(Vbar, reinterpret_cast<char*>(stage) + plane, plane, cudaMemcpyDeviceToHost, s->stream));
+  if (Ybar) HW_CUDA(cudaMemcpyAsync(Ybar, reinterpret_cast<char*>(stage) + 2 * plane, plane, cudaMemcpyDeviceToHost, s->stream));
+  HW_CUDA(cudaStreamSynchronize(s->stream));
+  return HW_OK;
+}
+
+hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes) {
+  if (!s || !bytes) return fail(HW_EINVAL, "null pointer");
+  *bytes = adjoint_layout(s).total;
+  return HW_OK;
+}
+
+hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Ubar_next, void* Ubar_n, void* scratch,
+                          size_t scratch_bytes) {
+  if (!s || !U_n || !Ubar_next || !Ubar_n || !scratch) return fail(HW_EINVAL, "null pointer");
+  if (s->eq != HW_EULER) return fail(HW_EINVAL, "the adjoint step is implemented for the Euler equations");
+  if (s->opt.positivity) return fail(HW_EINVAL, "the adjoint step does not cover the scale limiter");
+  if (!(dt > 0)) return fail(HW_EINVAL, "the adjoint step needs the (fixed) time step dt > 0");
+  const AdjointScratch L = adjoint_layout(s);
+  if (scratch_bytes < L.total) return fail(HW_ENOMEM, "scratch smaller than hw_adjoint_scratch_bytes");
+  if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return fail(HW_EINVAL, "scratch must be 256-byte aligned");
+  char* sb = static_cast<char*>(scratch);
+  DevScalars* asc = reinterpret_cast<DevScalars*>(sb + L.sc);
+  launch_reset(asc, 0.0, s->opt.cfl, s->stream);   // a private, never-done scalar block for the recomputation
+  StepArgs a = s->args(s->cur, dt);
+  a.U = U_n;
+  a.sc = asc;
+  launch_recon(s->prec, s->eq, a, s->stream);
+  AdjointArgs b{};
+  b.rgeo = a.rgeo;
+  b.igeo = a.igeo;
+  b.N = a.N;
+  b.ld = a.ld;
+  b.U = U_n;
+  b.Pb = a.Pb;
+  b.Ubar_next = Ubar_next;
+  b.Pbb = sb + L.Pbb;
+  b.Ubw = sb + L.Ubw;
+  b.Cb = sb + L.Cb;
+  b.Ubar = Ubar_n;
+  b.P = a.P;
+  b.dt = dt;
+  launch_adjoint(s->prec, b, s->stream);
+  HW_CUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+}  // extern "C"
+

@@ -92,6 +92,25 @@ struct BatchArgs {
   EqParams P;
 };
 
+// Arguments of the adjoint step (Euler; all state-like buffers are per-cell
+// records of the solver's internal layout).
+struct AdjointArgs {
+  const void* rgeo;
+  const int32_t* igeo;
+  int N;
+  int ld;
+  const void* U;           // state U^n
+  const void* Pb;          // forward edge-point data of U^n
+  const void* Ubar_next;   // cotangent of U^{n+1}
+  void* Pbb;               // scratch: cotangent of the edge-point data [ld][18m]
+  void* Ubw;               // scratch: direct cotangent of U^n [ld][3m]
+  void* Cb;                // scratch: stencil contributions [ld][4][3m]
+  void* Ubar;              // result: cotangent of U^n [ld][3m]
+  EqParams P;
+  double dt;
+};
+void launch_adjoint(int prec, const AdjointArgs& a, cudaStream_t st);
+
 // Resident blocks per SM of the batched kernel (cooperative launch limit).
 int batch_blocks_per_sm(int prec, int eq, bool lim);
 cudaError_t launch_batch(int prec, int eq, const BatchArgs& a, cudaStream_t st);

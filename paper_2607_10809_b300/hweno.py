@@ -28,7 +28,8 @@ EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_
             "hw_solver_destroy", "hw_last_error", "hw_step_static_scratch", "hw_batch_schedule_default",
             "hw_batch_workspace_bytes", "hw_batch_create", "hw_batch_set_schedule", "hw_batch_get_schedule",
             "hw_batch_autotune", "hw_batch_run_to", "hw_batch_steps", "hw_batch_reset", "hw_batch_get_state",
-            "hw_batch_destroy"]
+            "hw_batch_destroy", "hw_state_bytes", "hw_state_export", "hw_state_import", "hw_host_to_internal",
+            "hw_internal_to_host", "hw_adjoint_scratch_bytes", "hw_step_adjoint"]
 
 
 class HwError(RuntimeError):
@@ -97,6 +98,13 @@ def load():
         "hw_batch_reset": (ctypes.c_int, [vp]),
         "hw_batch_get_state": (ctypes.c_int, [vp, i32, vp, vp, vp, P(d), P(i64), P(i32)]),
         "hw_batch_destroy": (ctypes.c_int, [vp]),
+        "hw_state_bytes": (ctypes.c_int, [vp, P(sz)]),
+        "hw_state_export": (ctypes.c_int, [vp, vp]),
+        "hw_state_import": (ctypes.c_int, [vp, vp, d]),
+        "hw_host_to_internal": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "hw_internal_to_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "hw_adjoint_scratch_bytes": (ctypes.c_int, [vp, P(sz)]),
+        "hw_step_adjoint": (ctypes.c_int, [vp, d, vp, vp, vp, vp, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -241,6 +249,41 @@ class Solver:
         t = ctypes.c_double(); dt = ctypes.c_double(); n = ctypes.c_int64()
         _check(load().hw_time(self.h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(n)))
         return t.value, dt.value, n.value
+
+    # ---- device-side state buffers (internal order / precision, torch uint8 tensors)
+    def state_buffer(self):
+        import torch
+        n = ctypes.c_size_t()
+        _check(load().hw_state_bytes(self.h, ctypes.byref(n)))
+        return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+
+    def export_state(self, buf):
+        _check(load().hw_state_export(self.h, ctypes.c_void_p(buf.data_ptr())))
+
+    def import_state(self, buf, t=0.0):
+        _check(load().hw_state_import(self.h, ctypes.c_void_p(buf.data_ptr()), float(t)))
+
+    def host_to_internal(self, U, buf):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        _check(load().hw_host_to_internal(self.h, _ptr(U[0]), _ptr(U[1]), _ptr(U[2]), ctypes.c_void_p(buf.data_ptr())))
+
+    def internal_to_host(self, buf):
+        U = np.empty((3, self.m, self.mesh.nt))
+        _check(load().hw_internal_to_host(self.h, ctypes.c_void_p(buf.data_ptr()), _ptr(U[0]), _ptr(U[1]), _ptr(U[2])))
+        return U
+
+    def adjoint_scratch(self):
+        import torch
+        n = ctypes.c_size_t()
+        _check(load().hw_adjoint_scratch_bytes(self.h, ctypes.byref(n)))
+        return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+
+    def step_adjoint(self, dt, U_n, Ubar_next, Ubar_n, scratch):
+        """Ubar_n = (dU^{n+1}/dU^n)^T Ubar_next for a step of size dt (buffers:
+        state_buffer() tensors; scratch: adjoint_scratch())."""
+        _check(load().hw_step_adjoint(self.h, float(dt), ctypes.c_void_p(U_n.data_ptr()),
+                                      ctypes.c_void_p(Ubar_next.data_ptr()), ctypes.c_void_p(Ubar_n.data_ptr()),
+                                      ctypes.c_void_p(scratch.data_ptr()), scratch.numel()))
 
     def profile(self, enable=True):
         _check(load().hw_profile(self.h, int(enable)))

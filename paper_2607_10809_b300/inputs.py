@@ -364,6 +364,18 @@ def config5_mesh(n: int = 316) -> Mesh:
     return jittered_periodic(n, 10.0, jitter=0.15, seed=5)
 
 
+def config4_batch(count: int = 256):
+    """Batched Euler workload: `count` four-quadrant Riemann problems on [0, 1]^2,
+    each on its own jittered grid of 2k-40k triangles (transmissive
+    boundaries).  Returns (meshes, states)."""
+    meshes, states = [], []
+    for k, n in enumerate(config4_sizes(count)):
+        mesh = jittered_box(n, seed=4000 + k)
+        meshes.append(mesh)
+        states.append(initial_state(mesh, quadrant_fn(quadrant_states(4 + k)), 4, nq=4))
+    return meshes, states
+
+
 def config4_sizes(count: int = 256, seed: int = 4, lo: int = 2000, hi: int = 40000):
     """Triangle counts of the batched meshes, uniform in [lo, hi], as grid sizes n (2 n^2 triangles)."""
     rng = np.random.default_rng(seed)
