@@ -289,6 +289,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if not args.no_batch:
         line["batched"] = batched_leg(args, world)
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(args)
     if not args.no_cpu:
         rate, n, el = cpu_oracle_rate(mesh, U0, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -344,6 +346,71 @@ def batched_leg(args, world):
             "single_solve_sequential_seconds": seq_time}
 
 
+# ---------------------------------------------------------------- adjoint leg
+def adjoint_leg(args):
+    """Gradient of the density misfit J = 1/2 sum_K |K| (rho_K(T) - rho*_K)^2
+    with respect to the initial state (W, W_x, W_y averages), rho* the exact
+    unperturbed vortex at T, through `adj_steps` FP32 steps on the 199,712-cell
+    jittered periodic mesh of [0, 10]^2 (vortex + 8 density bumps), checkpoints
+    every 10 steps.  Reported: wall time of forward + backward (recompute and
+    adjoint steps) over the wall time of the plain forward, and the FP32
+    gradient's relative L-infinity difference to the FP64 gradient."""
+    import torch
+    from paper_2607_10809_b300 import hweno
+    from paper_2607_10809_b300.adjoint import cfl_steps, rollout
+    mesh = I.config5_mesh()
+    U0 = I.config5_state(mesh)
+    area = torch.from_numpy(I.cell_areas(mesh))
+    every = 10
+    out, grads = {}, {}
+    dts = None
+    for prec in ("fp32", "fp64"):
+        s = hweno.Solver(mesh, U0, eq="euler", precision=prec)
+        if dts is None:
+            dts = cfl_steps(s, U0, args.adj_steps)
+            T = float(np.sum(dts))
+            rho_star = torch.from_numpy(I.cell_averages(mesh, lambda x, y: I.vortex(x, y, T), 4)[0])
+
+        def forward():
+            s.set_state(U0, 0.0)
+            for dt in dts:
+                s.step(dt)
+            return s.get_state()[0]
+
+        def gradient():
+            x = torch.from_numpy(U0.copy()).requires_grad_(True)
+            UT = rollout(x, s, dts, every)
+            J = 0.5 * (area * (UT[0, 0] - rho_star) ** 2).sum()
+            J.backward()
+            return x.grad.numpy(), float(J)
+
+        def timed(fn, reps):
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = fn()
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            return statistics.median(ts), r
+
+        reps = 3 if prec == "fp32" else 1
+        forward(); gradient()                       # warm-up (graph/allocator/first-touch)
+        t_fwd, _ = timed(forward, reps)
+        t_adj, (g, J) = timed(gradient, reps)
+        grads[prec] = g
+        out[prec] = {"forward_s": t_fwd, "forward_backward_s": t_adj, "ratio": t_adj / t_fwd, "J": J}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    err = float(np.abs(grads["fp32"] - grads["fp64"]).max() / np.abs(grads["fp64"]).max())
+    return {"workload": f"euler vortex + 8 density bumps, jittered periodic [0,10]^2, {mesh.nt} triangles, "
+                        f"{len(dts)} steps, checkpoint every {every}",
+            "metric": "adjoint/forward wall time", "value": out["fp32"]["ratio"], "unit": "x",
+            "higher_is_better": False, "fp32": out["fp32"], "fp64": out["fp64"],
+            "grad_fp32_vs_fp64_rel_linf": err}
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The FP64 CPU oracle as the reference arm: each step is one oracle step
@@ -389,6 +456,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (many solves) leg")
     ap.add_argument("--batch-solves", type=int, default=256)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
+    ap.add_argument("--adj-steps", type=int, default=200)
     ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64"], help="precisions to run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-cells", type=int, default=4000)

@@ -189,7 +189,10 @@ hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, doubl
  * forward Taylor data of U_n are recomputed.  Non-smooth points (|.| in the
  * nonlinear weights and the viscosity, max in the viscosity) follow the
  * branch of the forward evaluation.  scratch: device memory of
- * hw_adjoint_scratch_bytes(), 256-byte aligned.  Asynchronous on the stream. */
+ * hw_adjoint_scratch_bytes(), 256-byte aligned.  Asynchronous on the stream.
+ * Errors: HW_EINVAL (null pointer, a state buffer not 16-byte aligned,
+ * scratch not 256-byte aligned, dt <= 0, not the Euler equations, scale
+ * limiter on), HW_ENOMEM (scratch_bytes too small). */
 hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes);
 hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Ubar_next, void* Ubar_n, void* scratch,
                           size_t scratch_bytes);

@@ -152,6 +152,7 @@ struct hw_solver {
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
     a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
     for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
+    eq_params_finish(a.P);
     return a;
   }
 };
@@ -586,6 +587,8 @@ hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* 
   if (s->eq != HW_EULER) return fail(HW_EINVAL, "the adjoint step is implemented for the Euler equations");
   if (s->opt.positivity) return fail(HW_EINVAL, "the adjoint step does not cover the scale limiter");
   if (!(dt > 0)) return fail(HW_EINVAL, "the adjoint step needs the (fixed) time step dt > 0");
+  if ((reinterpret_cast<uintptr_t>(U_n) | reinterpret_cast<uintptr_t>(Ubar_next) | reinterpret_cast<uintptr_t>(Ubar_n)) % 16)
+    return fail(HW_EINVAL, "state buffers must be 16-byte aligned");
   const AdjointScratch L = adjoint_layout(s);
   if (scratch_bytes < L.total) return fail(HW_ENOMEM, "scratch smaller than hw_adjoint_scratch_bytes");
   if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return fail(HW_EINVAL, "scratch must be 256-byte aligned");

@@ -129,6 +129,7 @@ struct hw_batch {
     a.grid = std::max(1, std::min(bps * sms, plan.ntiles));
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
     for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
+    eq_params_finish(a.P);
     a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
     return a;
   }

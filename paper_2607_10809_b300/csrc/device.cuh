@@ -2,6 +2,7 @@
 // the per-cell reconstruction (Section 2.2), the Lax-Wendroff procedure
 // (Section 2.1) and the flux functions.  Included by the kernel files only.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -28,6 +29,31 @@ struct EqParams {
   double ax, ay, gam, eps;
   double g[4];
   int positivity;   // scale limiter on (Euler)
+  // derived on the host by eq_params_finish: gamma - 1, |a|, and every
+  // constant rounded once to float for the single-precision kernels (a
+  // conversion or a double operation inside a kernel runs on the slow
+  // double-precision pipe)
+  double gm1, amag;
+  float axf, ayf, gamf, gm1f, epsf, amagf, gf[4];
+};
+
+inline void eq_params_finish(EqParams& P) {
+  P.gm1 = P.gam - 1.0;
+  P.amag = std::sqrt(P.ax * P.ax + P.ay * P.ay);
+  P.axf = (float)P.ax; P.ayf = (float)P.ay; P.gamf = (float)P.gam; P.gm1f = (float)P.gm1;
+  P.epsf = (float)P.eps; P.amagf = (float)P.amag;
+  for (int l = 0; l < 4; ++l) P.gf[l] = (float)P.g[l];
+}
+
+// the constants in the working precision R
+template <typename R> struct EqC {
+  static __device__ __forceinline__ R ax(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.ax; else return P.axf; }
+  static __device__ __forceinline__ R ay(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.ay; else return P.ayf; }
+  static __device__ __forceinline__ R gam(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.gam; else return P.gamf; }
+  static __device__ __forceinline__ R gm1(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.gm1; else return P.gm1f; }
+  static __device__ __forceinline__ R eps(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.eps; else return P.epsf; }
+  static __device__ __forceinline__ R amag(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.amag; else return P.amagf; }
+  static __device__ __forceinline__ R g(const EqParams& P, int l) { if constexpr (sizeof(R) == 8) return P.g[l]; else return P.gf[l]; }
 };
 
 template <typename R> struct GeoView {
@@ -47,8 +73,9 @@ __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : 
 // ---------------------------------------------------------------- nonlinear weights
 // Step 5 (Eq. nonlinearweight) for one component; also returns nothing else.
 // In double the paper's expression is evaluated as written.
-__device__ __forceinline__ void nonlinear_weights(double Wave, const double beta[4], const double g[4], double eps,
-                                                  double om[4]) {
+__device__ __forceinline__ void nonlinear_weights(double Wave, const double beta[4], const EqParams& P, double om[4]) {
+  const double* g = P.g;
+  const double eps = P.eps;
   const double tau = fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]) + fabs(beta[0] - beta[3]);
   const double kappa = tau * tau / 9.0;
   const double W2 = Wave * Wave, W4 = W2 * W2;
@@ -63,24 +90,23 @@ __device__ __forceinline__ void nonlinear_weights(double Wave, const double beta
 // normal float; below that (|W_ave| < 2^-20) the terms cannot be represented in
 // float and the expression is evaluated in double.  A non-finite sum falls back
 // to the linear weights.
-__device__ __forceinline__ void nonlinear_weights(float Wave, const float beta[4], const double g[4], double eps,
-                                                  float om[4]) {
+__device__ __forceinline__ void nonlinear_weights(float Wave, const float beta[4], const EqParams& P, float om[4]) {
   if (fabsf(Wave) < 9.5367431640625e-07f) {
     double bd[4] = {beta[0], beta[1], beta[2], beta[3]}, od[4];
-    nonlinear_weights((double)Wave, bd, g, eps, od);
+    nonlinear_weights((double)Wave, bd, P, od);
 #pragma unroll
     for (int l = 0; l < 4; ++l) om[l] = (float)od[l];
     return;
   }
   const float tau = fabsf(beta[0] - beta[1]) + fabsf(beta[0] - beta[2]) + fabsf(beta[0] - beta[3]);
   const float kappa = tau * tau * (1.0f / 9.0f);
-  const float W2 = Wave * Wave, W4e = W2 * W2 * (float)eps;
+  const float W2 = Wave * Wave, W4e = W2 * W2 * P.epsf;
   float wb[4], s = 0.f;
 #pragma unroll
-  for (int l = 0; l < 4; ++l) { wb[l] = (float)g[l] * (1.0f + kappa / (W4e + W2 * beta[l])); s += wb[l]; }
+  for (int l = 0; l < 4; ++l) { wb[l] = P.gf[l] * (1.0f + kappa / (W4e + W2 * beta[l])); s += wb[l]; }
   if (!isfinite(s) || s <= 0.f) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) om[l] = (float)g[l];
+    for (int l = 0; l < 4; ++l) om[l] = P.gf[l];
     return;
   }
   const float is = 1.0f / s;
@@ -133,12 +159,12 @@ __device__ __forceinline__ void reconstruct_component(const GA& ga, const R W0, 
   // Step 5
   const R Wave = (W0 + Wl[0] + Wl[1] + Wl[2]) * R(0.25) + R(1e-30);
   R om[4];
-  nonlinear_weights(Wave, beta, P.g, P.eps, om);
+  nonlinear_weights(Wave, beta, P, om);
   // Step 6: q = (om1/g1) p1 + sum_l (om_l - om1 g_l / g1) p_l
-  const R a1 = om[0] / R(P.g[0]);
+  const R a1 = om[0] / EqC<R>::g(P, 0);
   R al[3];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) al[l] = om[l + 1] - a1 * R(P.g[l + 1]);
+  for (int l = 0; l < 3; ++l) al[l] = om[l + 1] - a1 * EqC<R>::g(P, l + 1);
   R q1 = a1 * cc[0], q2 = a1 * cc[1];
 #pragma unroll
   for (int l = 0; l < 3; ++l) { q1 += al[l] * b[l][0]; q2 += al[l] * b[l][1]; }
@@ -205,7 +231,7 @@ template <typename R, int EQ>
 __device__ __forceinline__ void lax_wendroff(const R* W, const R* Wx, const R* Wy, const R* Wxx, const R* Wxy,
                                              const R* Wyy, const EqParams& P, R* Wt, R* Wtt) {
   if constexpr (EQ == kEqAdvection) {
-    const R ax = R(P.ax), ay = R(P.ay);
+    const R ax = EqC<R>::ax(P), ay = EqC<R>::ay(P);
     Wt[0] = -(ax * Wx[0] + ay * Wy[0]);
     Wtt[0] = ax * ax * Wxx[0] + R(2) * ax * ay * Wxy[0] + ay * ay * Wyy[0];
   } else if constexpr (EQ == kEqBurgers) {
@@ -217,7 +243,7 @@ __device__ __forceinline__ void lax_wendroff(const R* W, const R* Wx, const R* W
     Wt[0] = wt;
     Wtt[0] = -(wt * s + W[0] * (wtx + wty));
   } else {
-    const R gm1 = R(P.gam - 1.0);
+    const R gm1 = EqC<R>::gm1(P);
     Jet<R> J[4], f[4], g[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) J[c] = {W[c], Wx[c], Wy[c], Wxx[c], Wxy[c], Wyy[c], R(0), R(0), R(0)};
@@ -241,13 +267,13 @@ __device__ __forceinline__ void lax_wendroff(const R* W, const R* Wx, const R* W
 template <typename R, int EQ>
 __device__ __forceinline__ void flux_n(const R* W, R nx, R ny, const EqParams& P, R* H) {
   if constexpr (EQ == kEqAdvection) {
-    H[0] = (R(P.ax) * nx + R(P.ay) * ny) * W[0];
+    H[0] = (EqC<R>::ax(P) * nx + EqC<R>::ay(P) * ny) * W[0];
   } else if constexpr (EQ == kEqBurgers) {
     H[0] = R(0.5) * W[0] * W[0] * (nx + ny);
   } else {
     const R ir = R(1) / W[0];
     const R u = W[1] * ir, v = W[2] * ir;
-    const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
+    const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
     const R un = u * nx + v * ny;
     H[0] = W[0] * un;
     H[1] = W[1] * un + p * nx;
@@ -260,14 +286,14 @@ __device__ __forceinline__ void flux_n(const R* W, R nx, R ny, const EqParams& P
 template <typename R, int EQ>
 __device__ __forceinline__ R spectral_radius_n(const R* W, R nx, R ny, const EqParams& P) {
   if constexpr (EQ == kEqAdvection) {
-    return fabs(R(P.ax) * nx + R(P.ay) * ny);
+    return fabs(EqC<R>::ax(P) * nx + EqC<R>::ay(P) * ny);
   } else if constexpr (EQ == kEqBurgers) {
     return fabs(W[0] * (nx + ny));
   } else {
     const R ir = R(1) / W[0];
     const R u = W[1] * ir, v = W[2] * ir;
-    const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
-    return fabs(u * nx + v * ny) + sqrt(R(P.gam) * p * ir);
+    const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
+    return fabs(u * nx + v * ny) + sqrt(EqC<R>::gam(P) * p * ir);
   }
 }
 
@@ -276,14 +302,14 @@ __device__ __forceinline__ R spectral_radius_n(const R* W, R nx, R ny, const EqP
 template <typename R, int EQ>
 __device__ __forceinline__ R spectral_radius_all(const R* W, const EqParams& P) {
   if constexpr (EQ == kEqAdvection) {
-    return R(sqrt(P.ax * P.ax + P.ay * P.ay));
+    return EqC<R>::amag(P);
   } else if constexpr (EQ == kEqBurgers) {
     return R(1.4142135623730951) * fabs(W[0]);
   } else {
     const R ir = R(1) / W[0];
     const R u = W[1] * ir, v = W[2] * ir;
-    const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
-    return sqrt(u * u + v * v) + sqrt(R(P.gam) * p * ir);
+    const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
+    return sqrt(u * u + v * v) + sqrt(EqC<R>::gam(P) * p * ir);
   }
 }
 
@@ -336,7 +362,7 @@ template <typename R, int EQ> __device__ __forceinline__ bool physical(const R* 
   for (int c = 0; c < m; ++c) ok = ok && isfinite(W[c]);
   if constexpr (EQ == kEqEuler) {
     if (ok) {
-      const R p = R(P.gam - 1.0) * (W[3] - R(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+      const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
       ok = (W[0] > R(0)) && (p > R(0));
     }
   }

@@ -293,7 +293,7 @@ __device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap
         // scale limiter: spatial scaling over the six Gauss points, then the
         // Lax-Wendroff data, then scaling of the space-time Taylor data over
         // the points and the three time nodes
-        const R gam = R(P.gam);
+        const R gam = EqC<R>::gam(P);
         R Wb[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) Wb[c] = S.u[lc][c];

@@ -335,10 +335,15 @@ def vortex_bumps(seed: int, n: int = 8, amp: float = 0.01, sigma: float = 0.5, L
 
 
 # ----------------------------------------------------------------- errors
+def cell_areas(mesh: Mesh) -> np.ndarray:
+    """|K| of every triangle (counter-clockwise vertices)."""
+    P = mesh.unwrapped()
+    return 0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+
+
 def error_norms(mesh: Mesh, Wh: np.ndarray, We: np.ndarray):
     """L1 (area weighted) and L-infinity errors of cell averages (Section 3)."""
-    P = mesh.unwrapped()
-    area = 0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+    area = cell_areas(mesh)
     d = np.abs(Wh - We)
     return float((d * area).sum() / area.sum()), float(d.max())
 
@@ -362,6 +367,13 @@ def config3_mesh(target_points: int = 1_000_000, seed: int = 3) -> Mesh:
 def config5_mesh(n: int = 316) -> Mesh:
     """Euler on periodic [0, 10]^2, jittered grid, seed 5."""
     return jittered_periodic(n, 10.0, jitter=0.15, seed=5)
+
+
+def config5_state(mesh: Mesh, seed: int = 5) -> np.ndarray:
+    """Vortex plus 8 seeded Gaussian density bumps (amplitude 0.01, sigma 0.5):
+    the initial state of the gradient (adjoint) workload."""
+    bumps = vortex_bumps(seed)
+    return initial_state(mesh, lambda x, y: vortex(x, y, bumps=bumps), 4)
 
 
 def config4_batch(count: int = 256):
