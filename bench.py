@@ -353,7 +353,8 @@ def adjoint_leg(args):
     unperturbed vortex at T, through `adj_steps` FP32 steps on the 199,712-cell
     jittered periodic mesh of [0, 10]^2 (vortex + 8 density bumps), checkpoints
     every 10 steps.  Reported: wall time of forward + backward (recompute and
-    adjoint steps) over the wall time of the plain forward, and the FP32
+    adjoint steps) over the wall time of the plain forward (both from host
+    arrays to host arrays, outputs into pinned memory), and the FP32
     gradient's relative L-infinity difference to the FP64 gradient."""
     import torch
     from paper_2607_10809_b300 import hweno
@@ -371,18 +372,20 @@ def adjoint_leg(args):
             T = float(np.sum(dts))
             rho_star = torch.from_numpy(I.cell_averages(mesh, lambda x, y: I.vortex(x, y, T), 4)[0])
 
+        Uout = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
+
         def forward():
             s.set_state(U0, 0.0)
             for dt in dts:
                 s.step(dt)
-            return s.get_state()[0]
+            return s.get_state(out=Uout)[0]
 
         def gradient():
             x = torch.from_numpy(U0.copy()).requires_grad_(True)
             UT = rollout(x, s, dts, every)
             J = 0.5 * (area * (UT[0, 0] - rho_star) ** 2).sum()
             J.backward()
-            return x.grad.numpy(), float(J)
+            return x.grad.numpy(), float(J.detach())
 
         def timed(fn, reps):
             ts = []

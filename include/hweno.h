@@ -183,19 +183,30 @@ hw_status hw_state_import(hw_solver* s, const void* src, double t);
  * for cotangents); synchronise. */
 hw_status hw_host_to_internal(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, void* dst);
 hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, double* Vbar, double* Ybar);
+/* Edge-point buffer: the time-Taylor data (W, W_t, W_tt) of every cell at
+ * its six edge Gauss points, as a step computes them from the pre-step state
+ * (Section 2.1); hw_pb_bytes() bytes of device memory, 16-byte aligned.
+ * hw_step_keep is hw_step(s, dt) that leaves this data of the pre-step state
+ * in pb_out (written there in place of the solver's own buffer), so that the
+ * adjoint of the same step need not recompute it.  Not a step of the paper's
+ * method: the reverse pass of a checkpointed rollout uses it.  Errors:
+ * HW_EINVAL (null pointer, pb_out not 16-byte aligned). */
+hw_status hw_pb_bytes(const hw_solver* s, size_t* bytes);
+hw_status hw_step_keep(hw_solver* s, double dt, void* pb_out);
 /* Adjoint (vector-Jacobian product) of one step of size dt held fixed:
  * Ubar_n = (dU^{n+1}/dU^n)^T Ubar_next, for the Euler equations without the
- * scale limiter.  U_n, Ubar_next, Ubar_n: internal buffers (device); the
- * forward Taylor data of U_n are recomputed.  Non-smooth points (|.| in the
+ * scale limiter.  U_n, Ubar_next, Ubar_n: internal buffers (device).  Pb_n:
+ * the edge-point buffer hw_step_keep(s, dt, Pb_n) filled from U_n, or NULL to
+ * recompute it here.  Non-smooth points (|.| in the
  * nonlinear weights and the viscosity, max in the viscosity) follow the
  * branch of the forward evaluation.  scratch: device memory of
  * hw_adjoint_scratch_bytes(), 256-byte aligned.  Asynchronous on the stream.
- * Errors: HW_EINVAL (null pointer, a state buffer not 16-byte aligned,
- * scratch not 256-byte aligned, dt <= 0, not the Euler equations, scale
- * limiter on), HW_ENOMEM (scratch_bytes too small). */
+ * Errors: HW_EINVAL (null pointer, a state or edge-point buffer not
+ * 16-byte aligned, scratch not 256-byte aligned, dt <= 0, not the Euler
+ * equations, scale limiter on), HW_ENOMEM (scratch_bytes too small). */
 hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes);
-hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Ubar_next, void* Ubar_n, void* scratch,
-                          size_t scratch_bytes);
+hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Pb_n, const void* Ubar_next,
+                          void* Ubar_n, void* scratch, size_t scratch_bytes);
 
 /* ---------------------------------------------------------------------------
  * Batched runs: many independent solves (same options, meshes of any sizes)

@@ -21,7 +21,7 @@ class Rollout(torch.autograd.Function):
     def forward(ctx, U0, solver, dts, every):
         s = solver
         buf = s.state_buffer()
-        s.host_to_internal(U0.detach().cpu().numpy(), buf)
+        s.host_to_internal(np.asarray(U0.detach().cpu().numpy(), dtype=np.float64), buf)
         s.import_state(buf, 0.0)
         ckpts, times, t = [], [], 0.0
         for k, dt in enumerate(dts):
@@ -32,29 +32,37 @@ class Rollout(torch.autograd.Function):
                 times.append(t)
             s.step(float(dt))
             t += float(dt)
-        UT, _ = s.get_state()
+        UT = _host_tensor(U0.shape)
+        s.get_state(out=UT.numpy())
         ctx.solver, ctx.dts, ctx.every, ctx.ckpts, ctx.times = s, list(dts), every, ckpts, times
-        return torch.from_numpy(UT)
+        return UT
 
     @staticmethod
     def backward(ctx, gUT):
         s, dts, every = ctx.solver, ctx.dts, ctx.every
         ub = s.state_buffer()
-        s.host_to_internal(gUT.detach().cpu().numpy().astype(np.float64), ub)
+        s.host_to_internal(np.asarray(gUT.detach().cpu().numpy(), dtype=np.float64), ub)
         ubn = s.state_buffer()
         scratch = s.adjoint_scratch()
         states = [s.state_buffer() for _ in range(every)]
+        pbs = [s.pb_buffer() for _ in range(every)]
         for seg in reversed(range(len(ctx.ckpts))):
             start, end = seg * every, min((seg + 1) * every, len(dts))
             s.import_state(ctx.ckpts[seg], ctx.times[seg])
-            for k in range(start, end):          # recompute the segment's states
+            for k in range(start, end):          # recompute the segment's states and edge-point data
                 s.export_state(states[k - start])
-                s.step(float(dts[k]))
+                s.step_keep(float(dts[k]), pbs[k - start])
             for k in reversed(range(start, end)):
-                s.step_adjoint(float(dts[k]), states[k - start], ub, ubn, scratch)
+                s.step_adjoint(float(dts[k]), states[k - start], ub, ubn, scratch, pbs[k - start])
                 ub, ubn = ubn, ub
-        g0 = s.internal_to_host(ub)
-        return torch.from_numpy(g0), None, None, None
+        g0 = _host_tensor(gUT.shape)
+        s.internal_to_host(ub, out=g0.numpy())
+        return g0, None, None, None
+
+
+def _host_tensor(shape):
+    """float64 CPU tensor in pinned memory (direct device-to-host copies)."""
+    return torch.empty(tuple(shape), dtype=torch.float64, pin_memory=True)
 
 
 def rollout(U0, solver, dts, every=10):

@@ -508,15 +508,13 @@ namespace {
 size_t state_bytes(const hw_solver* s) { return (size_t)3 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4); }
 
 struct AdjointScratch {
-  size_t Pbb, Ubw, Cb, sc, total;
+  size_t Cb, sc, total;
 };
 AdjointScratch adjoint_layout(const hw_solver* s) {
   const size_t es = s->prec == HW_FP64 ? 8 : 4, ld = (size_t)s->ld, m = (size_t)s->m;
   AdjointScratch a{};
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
-  a.Pbb = take(18 * m * ld * es);
-  a.Ubw = take(3 * m * ld * es);
   a.Cb = take(12 * m * ld * es);
   a.sc = take(sizeof(DevScalars));
   a.total = o;
@@ -575,30 +573,52 @@ hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, doubl
   return HW_OK;
 }
 
+hw_status hw_pb_bytes(const hw_solver* s, size_t* bytes) {
+  if (!s || !bytes) return fail(HW_EINVAL, "null pointer");
+  *bytes = (size_t)18 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4);
+  return HW_OK;
+}
+
+hw_status hw_step_keep(hw_solver* s, double dt, void* pb_out) {
+  if (!s || !pb_out) return fail(HW_EINVAL, "null pointer");
+  if (reinterpret_cast<uintptr_t>(pb_out) % 16) return fail(HW_EINVAL, "edge-point buffer must be 16-byte aligned");
+  StepArgs a = s->args(s->cur, dt > 0 ? dt : 0.0);
+  a.Pb = pb_out;
+  launch_step(s->prec, s->eq, a, s->stream);
+  HW_CUDA(cudaGetLastError());
+  s->cur = 1 - s->cur;
+  return HW_OK;
+}
+
 hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes) {
   if (!s || !bytes) return fail(HW_EINVAL, "null pointer");
   *bytes = adjoint_layout(s).total;
   return HW_OK;
 }
 
-hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Ubar_next, void* Ubar_n, void* scratch,
-                          size_t scratch_bytes) {
+hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Pb_n, const void* Ubar_next,
+                          void* Ubar_n, void* scratch, size_t scratch_bytes) {
   if (!s || !U_n || !Ubar_next || !Ubar_n || !scratch) return fail(HW_EINVAL, "null pointer");
   if (s->eq != HW_EULER) return fail(HW_EINVAL, "the adjoint step is implemented for the Euler equations");
   if (s->opt.positivity) return fail(HW_EINVAL, "the adjoint step does not cover the scale limiter");
   if (!(dt > 0)) return fail(HW_EINVAL, "the adjoint step needs the (fixed) time step dt > 0");
-  if ((reinterpret_cast<uintptr_t>(U_n) | reinterpret_cast<uintptr_t>(Ubar_next) | reinterpret_cast<uintptr_t>(Ubar_n)) % 16)
-    return fail(HW_EINVAL, "state buffers must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(U_n) | reinterpret_cast<uintptr_t>(Pb_n) | reinterpret_cast<uintptr_t>(Ubar_next) |
+       reinterpret_cast<uintptr_t>(Ubar_n)) % 16)
+    return fail(HW_EINVAL, "state and edge-point buffers must be 16-byte aligned");
   const AdjointScratch L = adjoint_layout(s);
   if (scratch_bytes < L.total) return fail(HW_ENOMEM, "scratch smaller than hw_adjoint_scratch_bytes");
   if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return fail(HW_EINVAL, "scratch must be 256-byte aligned");
   char* sb = static_cast<char*>(scratch);
-  DevScalars* asc = reinterpret_cast<DevScalars*>(sb + L.sc);
-  launch_reset(asc, 0.0, s->opt.cfl, s->stream);   // a private, never-done scalar block for the recomputation
   StepArgs a = s->args(s->cur, dt);
   a.U = U_n;
-  a.sc = asc;
-  launch_recon(s->prec, s->eq, a, s->stream);
+  if (Pb_n) {
+    a.Pb = const_cast<void*>(Pb_n);   // read only below
+  } else {
+    DevScalars* asc = reinterpret_cast<DevScalars*>(sb + L.sc);
+    launch_reset(asc, 0.0, s->opt.cfl, s->stream);   // a private, never-done scalar block for the recomputation
+    a.sc = asc;
+    launch_recon(s->prec, s->eq, a, s->stream);
+  }
   AdjointArgs b{};
   b.rgeo = a.rgeo;
   b.igeo = a.igeo;
@@ -607,8 +627,6 @@ hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* 
   b.U = U_n;
   b.Pb = a.Pb;
   b.Ubar_next = Ubar_next;
-  b.Pbb = sb + L.Pbb;
-  b.Ubw = sb + L.Ubw;
   b.Cb = sb + L.Cb;
   b.Ubar = Ubar_n;
   b.P = a.P;

@@ -102,8 +102,6 @@ struct AdjointArgs {
   const void* U;           // state U^n
   const void* Pb;          // forward edge-point data of U^n
   const void* Ubar_next;   // cotangent of U^{n+1}
-  void* Pbb;               // scratch: cotangent of the edge-point data [ld][18m]
-  void* Ubw;               // scratch: direct cotangent of U^n [ld][3m]
   void* Cb;                // scratch: stencil contributions [ld][4][3m]
   void* Ubar;              // result: cotangent of U^n [ld][3m]
   EqParams P;

@@ -29,7 +29,7 @@ EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_
             "hw_batch_workspace_bytes", "hw_batch_create", "hw_batch_set_schedule", "hw_batch_get_schedule",
             "hw_batch_autotune", "hw_batch_run_to", "hw_batch_steps", "hw_batch_reset", "hw_batch_get_state",
             "hw_batch_destroy", "hw_state_bytes", "hw_state_export", "hw_state_import", "hw_host_to_internal",
-            "hw_internal_to_host", "hw_adjoint_scratch_bytes", "hw_step_adjoint"]
+            "hw_internal_to_host", "hw_pb_bytes", "hw_step_keep", "hw_adjoint_scratch_bytes", "hw_step_adjoint"]
 
 
 class HwError(RuntimeError):
@@ -104,7 +104,9 @@ def load():
         "hw_host_to_internal": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "hw_internal_to_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "hw_adjoint_scratch_bytes": (ctypes.c_int, [vp, P(sz)]),
-        "hw_step_adjoint": (ctypes.c_int, [vp, d, vp, vp, vp, vp, sz]),
+        "hw_pb_bytes": (ctypes.c_int, [vp, P(sz)]),
+        "hw_step_keep": (ctypes.c_int, [vp, d, vp]),
+        "hw_step_adjoint": (ctypes.c_int, [vp, d, vp, vp, vp, vp, vp, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -267,10 +269,24 @@ class Solver:
         U = np.ascontiguousarray(U, dtype=np.float64)
         _check(load().hw_host_to_internal(self.h, _ptr(U[0]), _ptr(U[1]), _ptr(U[2]), ctypes.c_void_p(buf.data_ptr())))
 
-    def internal_to_host(self, buf):
-        U = np.empty((3, self.m, self.mesh.nt))
+    def internal_to_host(self, buf, out=None):
+        """``out``: optional float64 array [3, m, nt] (pinned memory makes the
+        device-to-host copy direct)."""
+        U = np.empty((3, self.m, self.mesh.nt)) if out is None else out
+        assert U.shape == (3, self.m, self.mesh.nt) and U.dtype == np.float64 and U.flags.c_contiguous
         _check(load().hw_internal_to_host(self.h, ctypes.c_void_p(buf.data_ptr()), _ptr(U[0]), _ptr(U[1]), _ptr(U[2])))
         return U
+
+    def pb_buffer(self):
+        """Edge-point buffer (torch uint8 tensor) for step_keep / step_adjoint."""
+        import torch
+        n = ctypes.c_size_t()
+        _check(load().hw_pb_bytes(self.h, ctypes.byref(n)))
+        return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+
+    def step_keep(self, dt, pb):
+        """hw_step that leaves the edge-point data of the pre-step state in pb."""
+        _check(load().hw_step_keep(self.h, float(dt), ctypes.c_void_p(pb.data_ptr())))
 
     def adjoint_scratch(self):
         import torch
@@ -278,10 +294,12 @@ class Solver:
         _check(load().hw_adjoint_scratch_bytes(self.h, ctypes.byref(n)))
         return torch.empty(n.value, dtype=torch.uint8, device="cuda")
 
-    def step_adjoint(self, dt, U_n, Ubar_next, Ubar_n, scratch):
+    def step_adjoint(self, dt, U_n, Ubar_next, Ubar_n, scratch, pb=None):
         """Ubar_n = (dU^{n+1}/dU^n)^T Ubar_next for a step of size dt (buffers:
-        state_buffer() tensors; scratch: adjoint_scratch())."""
+        state_buffer() tensors; scratch: adjoint_scratch(); pb: the
+        pb_buffer() that step_keep(dt, pb) filled from U_n, or None)."""
         _check(load().hw_step_adjoint(self.h, float(dt), ctypes.c_void_p(U_n.data_ptr()),
+                                      ctypes.c_void_p(pb.data_ptr() if pb is not None else None),
                                       ctypes.c_void_p(Ubar_next.data_ptr()), ctypes.c_void_p(Ubar_n.data_ptr()),
                                       ctypes.c_void_p(scratch.data_ptr()), scratch.numel()))
 

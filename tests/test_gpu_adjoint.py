@@ -128,3 +128,26 @@ def test_adjoint_rejects_unsupported_configurations():
     with pytest.raises(hweno.HwError) as e:
         s.step_adjoint(0.01, a, b, a, s.adjoint_scratch())
     assert e.value.status == hweno.HW_EINVAL
+
+
+def test_kept_edge_point_data_equals_the_recomputed_one():
+    """hw_step_keep leaves the step unchanged and its edge-point data make
+    hw_step_adjoint give bit-for-bit the result of the recomputing path."""
+    mesh = I.jittered_periodic(11, 10.0, 0.15, seed=33)
+    U0 = bumped_vortex(mesh)
+    for prec in ("fp64", "fp32"):
+        s = hweno.Solver(mesh, U0, eq="euler", precision=prec)
+        dt = 0.5 * s.time()[1]
+        s.step(dt)
+        U1_plain, _ = s.get_state()
+        s.set_state(U0, 0.0)
+        un, pb = s.state_buffer(), s.pb_buffer()
+        s.export_state(un)
+        s.step_keep(dt, pb)
+        U1_keep, _ = s.get_state()
+        assert np.array_equal(U1_plain, U1_keep), prec
+        ub, a, b, scratch = s.state_buffer(), s.state_buffer(), s.state_buffer(), s.adjoint_scratch()
+        s.host_to_internal(np.random.default_rng(4).normal(size=U0.shape), ub)
+        s.step_adjoint(dt, un, ub, a, scratch)
+        s.step_adjoint(dt, un, ub, b, scratch, pb)
+        assert np.array_equal(s.internal_to_host(a), s.internal_to_host(b)), prec
