@@ -205,10 +205,14 @@ __device__ __forceinline__ unsigned char* smem_base(unsigned char* raw) {
 // Reconstruction + Lax-Wendroff over the context's tiles (double-buffered TMA
 // staging).  bar: two initialised mbarriers, ph: their phase bits (kept across
 // calls).  Returns false if a bounded wait gave up (flag 2 raised).
-template <typename R, int EQ, bool LIM, typename Ctx>
+// NT: threads of the block.  Phase A runs the (cell, component) tasks and
+// phase B the (cell, point) tasks in passes of NT; the limiter's phase B
+// synchronises per point and needs one thread per (cell, point).
+template <typename R, int EQ, bool LIM, int NT, typename Ctx>
 __device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap* mIdx, const EqParams& P,
                             R* __restrict__ Pb, unsigned char* base, uint64_t* bar, unsigned* ph) {
   constexpr int m = EqTraits<EQ>::m;
+  static_assert(!LIM || NT == 6 * kCells, "the limiter path takes one thread per (cell, point)");
   using Stage = ReconStage<R, EQ>;
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*qs)[6][kCells] = reinterpret_cast<R (*)[6][kCells]>(base + 2 * sizeof(Stage));
@@ -250,8 +254,8 @@ __device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap
     const R* U = ctx.uin(tile);
     const R dtr = R(ctx.dt_of(tile));   // time nodes of the limiter
     const Stage& S = st[s];
-    if (t < m * kCells) {
-      const int lc = t % kCells, c = t / kCells;
+    for (int task = t; task < m * kCells; task += NT) {
+      const int lc = task % kCells, c = task / kCells;
       if (lc < count) {
         R Wl[3], Vl[3], Yl[3];
         const R* own = S.u[lc];
@@ -269,8 +273,8 @@ __device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap
       }
     }
     __syncthreads();
-    {
-      const int lc = t % kCells, qp = t / kCells, i = cell0 + lc;
+    for (int task = t; task < 6 * kCells; task += NT) {
+      const int lc = task % kCells, qp = task / kCells, i = cell0 + lc;
       const bool act = lc < count;
       R W[m], Wx[m], Wy[m], Wxx[m], Wxy[m], Wyy[m], Wt[m], Wtt[m];
       if (act) {
@@ -547,7 +551,7 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
 
 // ---------------------------------------------------------------- single-solve kernels
 template <typename R, int EQ, bool LIM>
-__global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUtensorMap mGeo,
+__global__ void __launch_bounds__(LIM ? kThreads : kLeanThreads) k_recon(const __grid_constant__ CUtensorMap mGeo,
                                                      const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
                                                      const R* __restrict__ U, R* __restrict__ Pb, EqParams P,
                                                      DevScalars* sc, double dt_fixed, TileSet ts) {
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_recon(const __grid_constant__ CUte
   }
   __syncthreads();
   unsigned ph[2] = {0u, 0u};
-  recon_phase<R, EQ, LIM>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
+  recon_phase<R, EQ, LIM, LIM ? kThreads : kLeanThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
 }
 
 template <typename R, int EQ>
@@ -672,7 +676,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUte
   bool ok = true;
   for (int step = 0; step < max_steps && ok; ++step) {
     const int slot = step & 1;
-    ok = recon_phase<R, EQ, LIM>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
+    ok = recon_phase<R, EQ, LIM, kThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
     if (!grid_barrier(ctl, spin_limit, skip || !ok)) ok = false;
     if (!ok) break;
     ok = edge_phase<R, EQ>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph);
@@ -854,21 +858,21 @@ __global__ void k_batch_reset_ctl(BatchCtl* ctl) {
 namespace {
 // Resident blocks of a kernel on the current device (occupancy x SMs); the
 // launches use min(tiles, this) blocks.
-template <typename K> int resident_blocks(K kernel, size_t smem) {
+template <typename K> int resident_blocks(K kernel, int threads, size_t smem) {
   int dev = 0, sms = 148, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   return sms * (per_sm > 0 ? per_sm : 1);
 }
 
 template <typename R, int EQ, bool LIM> int recon_cap() {
-  static const int cap = resident_blocks(k_recon<R, EQ, LIM>, recon_smem_bytes<R, EQ>());
+  static const int cap = resident_blocks(k_recon<R, EQ, LIM>, LIM ? kThreads : kLeanThreads, recon_smem_bytes<R, EQ>());
   return cap;
 }
 template <typename R, int EQ> int edge_cap() {
-  static const int cap = resident_blocks(k_edge<R, EQ>, edge_smem_bytes<R, EQ>());
+  static const int cap = resident_blocks(k_edge<R, EQ>, kThreads, edge_smem_bytes<R, EQ>());
   return cap;
 }
 template <typename R, int EQ> void prepare_t() {
@@ -882,7 +886,7 @@ template <typename R, int EQ, bool LIM> void launch_recon_lim(const StepArgs& a,
   constexpr size_t smem = recon_smem_bytes<R, EQ>();
   const int cap = recon_cap<R, EQ, LIM>();
   const int nt = a.tiles.ntiles;
-  k_recon<R, EQ, LIM><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
+  k_recon<R, EQ, LIM><<<nt < cap ? (nt > 0 ? nt : 1) : cap, LIM ? kThreads : kLeanThreads, smem, st>>>(
       a.maps->geo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Pb), a.P, a.sc,
       a.dt_fixed, a.tiles);
 }

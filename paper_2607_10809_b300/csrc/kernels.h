@@ -12,7 +12,10 @@ namespace hw {
 
 constexpr int kConsvBlocks = 296;                  // 2 x 148 SMs, fixed so the summation order is fixed
 constexpr int kCells = 32;                         // cells per tile; plane strides are multiples of it
-constexpr int kThreads = 6 * kCells;               // 6 threads per cell
+constexpr int kThreads = 6 * kCells;               // 6 threads per cell (batched kernel, scale limiter)
+constexpr int kLeanThreads = 2 * kCells;           // single-solve reconstruction: 2 threads per cell, so
+                                                   // that the (cell, component) and (cell, point) task sets
+                                                   // of a tile fill whole passes (2 and 3 for the Euler system)
 constexpr int kReconPlanes = G_IH + 1;             // geometry planes 0 .. G_IH feed the reconstruction
 constexpr int kEdgePlanes = NRGEO - G_NRM;         // planes G_NRM .. G_INR feed the flux kernel
 
