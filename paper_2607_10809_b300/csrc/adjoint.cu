@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_step(AdjPtrs a, R* __restri
       if (i < N) {
         const int j = qp >> 1, g = qp & 1, jn = (j + 1) % 3;
         const int nb = B.nb[j][lc];
-        const bool left = (nb < 0) || (i < nb);
+        const bool left = (B.nb[3][lc] >> (6 + j)) & 1;   // this cell owns the edge: canonical left side
         const R nx = B.geo[G_NRM + 2 * j][lc], ny = B.geo[G_NRM + 2 * j + 1][lc];
         const R el = B.geo[G_EL + j][lc];
         // (a) edge: reverse of the Lobatto sum of the LLF flux and of Eq. timeflux

@@ -29,7 +29,8 @@ enum RGeo : int {
 // Per-cell integer planes.
 enum IGeo : int {
   I_NBR = 0,   // 3: neighbour across local edge j (internal numbering), -1 on a boundary
-  I_NBE = 3,   // 1: packed neighbour local edge indices, 2 bits per edge
+  I_NBE = 3,   // 1: packed: bits 2j, 2j+1: the neighbour's local index of edge j; bit 6 + j: this cell
+               //    owns edge j (lower index in the caller's numbering, or a boundary edge)
   NIGEO = 4
 };
 

@@ -444,12 +444,12 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
     const R dtr = R(ctx.dt_of(tile));
     const Stage& S = st[s];
     {
-      const int lc = t % kCells, qp = t / kCells, i = cell0 + lc;
+      const int lc = t % kCells, qp = t / kCells;
       if (lc < count) {
         const int j = qp >> 1, gm = qp & 1;
         const int nb = S.idx[j][lc];
         const int je = (S.idx[3][lc] >> (2 * j)) & 3;
-        const bool left = (nb < 0) || (i < nb);
+        const bool left = (S.idx[3][lc] >> (6 + j)) & 1;   // this cell owns the edge: canonical left side
         const R nx = S.geo[2 * j][lc], ny = S.geo[2 * j + 1][lc];
         const R el = S.geo[6 + j][lc];
         R Wi[m], Wn[m];

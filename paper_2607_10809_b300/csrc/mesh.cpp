@@ -189,6 +189,7 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
         Au = A[u];
         I(I_NBR + j, k) = M.inv[u];
         packed |= (M.nbe_orig[3 * t + j] & 3) << (2 * j);
+        if (t < u) packed |= 1 << (6 + j);   // this cell owns the edge (lower index in the caller's numbering)
       } else {
         // transmissive ghost: K0 reflected across edge j (it carries K0's data)
         const double ax = X0[j], ay = Y0[j], bx = X0[(j + 1) % 3], by = Y0[(j + 1) % 3];
@@ -199,6 +200,7 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
         }
         Au = A0;
         I(I_NBR + j, k) = -1;
+        packed |= 1 << (6 + j);   // a boundary edge belongs to its cell
       }
       double mu[5];
       tri_moments(X, Y, mu);
@@ -297,12 +299,16 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
     }
   }
 
-  // ---- edge geometry: canonical normal (outward of the lower internal index)
+  // ---- edge geometry: canonical normal, outward of the edge's owner, the
+  // cell with the lower index in the caller's numbering, and computed in the
+  // owner's frame: every edge gets one normal and one length whatever the
+  // renumbering (on a periodic seam the two cells' frames differ by a shift
+  // that is not exact in floating point)
   for (int64_t k = 0; k < nt; ++k) {
     const int64_t t = M.perm[k];
     for (int j = 0; j < 3; ++j) {
       const int32_t un = I(I_NBR + j, k);
-      const bool left = (un < 0) || (k < un);
+      const bool left = (un < 0) || (t < M.perm[un]);
       int64_t owner = left ? t : M.perm[un];
       int jo = left ? j : M.nbe_orig[3 * t + j];
       const double ax = VX[3 * owner + jo], ay = VY[3 * owner + jo];
