@@ -42,7 +42,13 @@
 //       spectral radius over all directions; last step clipped to T;
 //   R13 non-periodic boundaries are transmissive: the ghost cell is the mirror
 //       image of the cell with the cell's own data, and W^ext = W^int on the
-//       boundary edge.
+//       boundary edge;
+//   R18 the scale limiter (optional, Euler): Zhang-Shu positivity scaling of
+//       the final reconstruction toward the cell average over the six edge
+//       Gauss points (density first, then pressure through the smallest
+//       non-negative root of a quadratic, clamped to 1), eps = min(1e-13,
+//       rho_bar, p_bar); then the same scaling of the space-time Taylor data
+//       over the points and the three time nodes.
 #include <algorithm>
 #include <array>
 #include <cmath>
