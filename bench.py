@@ -63,7 +63,7 @@ TRAFFIC = {
 
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "device.cuh", "internal.h"):
+    for f in ("kernels.cu", "kernels.h", "device.cuh", "tma.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2607_10809_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
