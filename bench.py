@@ -168,6 +168,32 @@ def cpu_oracle_rate(mesh, U0, target_seconds=12.0):
 
 
 # ---------------------------------------------------------------- our arm
+# ---------------------------------------------------------------- replicas (N > 1)
+# One independent replica per rank; the only collectives are the barriers
+# around the timed region and the max over ranks of its duration.
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+def max_over_ranks_of(x, world, device):
+    """max over ranks of a float (NCCL: device "cuda"; gloo: "cpu")."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(cells, steps, ms_max, world):
+    """Whole-job throughput: all ranks' triangle updates over the slowest
+    rank's time (weak scaling)."""
+    return world * cells * steps / (ms_max * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2607_10809_b300 import build as B
@@ -179,20 +205,12 @@ def run_ours(args, rank, world, local_rank):
     mesh, U0 = workload(args.workload)
     N = mesh.nt
     hmesh = hweno.Mesh(mesh)
-    dist = world > 1
-    if dist:
-        import torch.distributed as tdist
 
     def barrier():
-        if dist:
-            tdist.barrier()
+        dist_barrier(world)
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, "cuda")
 
     results = {}
     precs = ("fp32", "fp64") if args.only == "both" else (args.only,)
@@ -244,7 +262,7 @@ def run_ours(args, rank, world, local_rank):
     hbm, peak_kind = measured_peaks()
     r32 = results["fp32"]
     K = r32["K"]
-    value = world * N * K / (r32["ms"] * 1e-3)
+    value = replicas_value(N, K, r32["ms"], world)
     rec_ms = r32["prof"]["recon_ms"] / max(1, r32["prof"]["steps"])
     edge_ms = r32["prof"]["edge_ms"] / max(1, r32["prof"]["steps"])
     dom = "recon" if rec_ms >= edge_ms else "edge"
@@ -278,11 +296,11 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / hbm, "peak_kind": peak_kind, "alg_bytes_per_cell": alg_bytes(dom, 4),
                      "traffic": (tr * N) if tr else None,
                      "kernel_ms": {"k_recon": rec_ms, "k_edge": edge_ms}},
-        "e2e": {"value": world * N * e2e["steps"] / e2e["s"], "unit": UNIT,
+        "e2e": {"value": replicas_value(N, e2e["steps"], e2e["s"] * 1e3, world), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["bytes"], "d2h_bytes_per_step": e2e["bytes"]},
         "gpu_launches": 2 * K,
         "clocks": r32["clocks"],
-        "fp64": {"value": world * N * r64["K"] / (r64["ms"] * 1e-3), "steps": r64["K"],
+        "fp64": {"value": replicas_value(N, r64["K"], r64["ms"], world), "steps": r64["K"],
                  "ms_per_step": r64["ms"] / r64["K"], "kernel_ms": {"k_recon": rec64, "k_edge": edge64},
                  "clocks": r64["clocks"]},
         "status_flags": {"fp32": r32["flags"], "fp64": r64["flags"]},

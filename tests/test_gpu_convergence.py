@@ -1,0 +1,89 @@
+"""Convergence tables of the paper's three smooth examples, computed by the FP64
+GPU path on seeded jittered periodic meshes of about the paper's sizes:
+Burgers (Example 3.1, Table ex4.1, T = 0.5/pi), the Euler density wave
+(Example 3.2, Table ex4.12d, T = 1) and the isentropic vortex (Example 3.3,
+Table isotro, T = 1).  The paper's meshes are not available, so the observed
+orders and the rough error magnitudes are compared with the printed ones
+(tests/golden/paper_convergence.json); the coarsest mesh of each table is also
+run through the oracle to 1e-12."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_10809_b300 import build as B
+from paper_2607_10809_b300 import hweno
+from paper_2607_10809_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    B.build()
+    hweno.load()
+
+
+# (golden key, equation, components, period, grid sizes n (2 n^2 triangles), initial data, exact solution at T, T)
+CASES = {
+    "burgers": ("burgers_L1", "burgers", 1, 4.0, [12, 23, 46, 93, 185, 370], I.burgers_sine,
+                lambda T: (lambda x, y: I.burgers_exact(x, y, T)), 0.5 / np.pi),
+    "density_wave": ("euler_wave_L1", "euler", 4, 4.0, [12, 23, 46, 93, 185], lambda x, y: I.density_wave(x, y),
+                     lambda T: (lambda x, y: I.density_wave(x, y, T)), 1.0),
+    "vortex": ("vortex_L1", "euler", 4, 10.0, [11, 22, 44, 88, 177], I.vortex,
+               lambda T: (lambda x, y: I.vortex(x, y, T)), 1.0),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_convergence_table(case, golden_dir):
+    key, eq, m, L, ns, fn, exact, T = CASES[case]
+    paper = json.load(open(os.path.join(golden_dir, "paper_convergence.json")))[key]
+    rows = []
+    for n in ns:
+        mesh = I.jittered_periodic(n, L, 0.15, seed=100 + n)
+        U0 = I.initial_state(mesh, fn, m)
+        s = hweno.Solver(mesh, U0, eq=eq, precision="fp64")
+        s.run_to(T)
+        W = s.get_state()[0][0][0]   # density (Euler) or u (Burgers)
+        s.close()
+        We = I.cell_averages(mesh, exact(T), m)[0]
+        l1, linf = I.error_norms(mesh, W, We)
+        rows.append((mesh.nt, l1, linf))
+    N = np.array([r[0] for r in rows], float)
+    e1 = np.array([r[1] for r in rows])
+    ei = np.array([r[2] for r in rows])
+    # h ~ N^(-1/2): order = log(e_k / e_k+1) / log(h_k / h_k+1)
+    o1 = np.log(e1[:-1] / e1[1:]) / (0.5 * np.log(N[1:] / N[:-1]))
+    oi = np.log(ei[:-1] / ei[1:]) / (0.5 * np.log(N[1:] / N[:-1]))
+    print(f"\n{case}, T = {T:.4f} (paper: {paper['cite']})")
+    print("   N        L1      order     Linf     order   | paper N     L1")
+    for k in range(len(rows)):
+        po = f"{o1[k - 1]:6.2f}" if k else "      "
+        pi = f"{oi[k - 1]:6.2f}" if k else "      "
+        pp = f"{paper['N'][k]:8d}  {paper['L1'][k]:.2e}" if k < len(paper["N"]) else ""
+        print(f"{int(N[k]):8d}  {e1[k]:.2e} {po}  {ei[k]:.2e} {pi}   | {pp}")
+    # third order at the fine levels, as in the paper's tables
+    assert np.all(o1[-2:] > 2.6) and np.all(o1[-2:] < 3.4), o1
+    # the same magnitude as the paper's errors at about the same sizes
+    k = min(len(rows), len(paper["N"])) - 1
+    assert 0.2 < e1[k] / paper["L1"][k] < 5.0, (e1[k], paper["L1"][k])
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_coarsest_mesh_of_the_table_matches_the_oracle(case):
+    key, eq, m, L, ns, fn, exact, T = CASES[case]
+    mesh = I.jittered_periodic(ns[0], L, 0.15, seed=100 + ns[0])
+    U0 = I.initial_state(mesh, fn, m)
+    s = hweno.Solver(mesh, U0, eq=eq, precision="fp64")
+    n = s.run_to(T)
+    Ug, t = s.get_state()
+    Uo, dts = oracle.Oracle(mesh, eq).run_to(U0, T)
+    assert n == len(dts) and abs(t - T) < 1e-14
+    err = (np.abs(Ug - Uo).max(axis=-1) / np.maximum(np.abs(Uo).max(axis=-1), 1e-300)).max()
+    print(f"{case}, {mesh.nt} triangles, {n} steps: relative Linf {err:.2e}")
+    assert err < 1e-12

@@ -160,3 +160,34 @@ def test_batch_256_solves_fp32_positivity_and_completion():
     print(f"batched FP32 run: {len(meshes) - failed} of {len(meshes)} solves reached T = {T}, {failed} failed")
     assert failed < len(meshes) // 10
     b.close()
+
+
+# Full runs at the benchmark sizes: the FP32 form against the FP64 form (the
+# oracle itself cannot run 2M triangles for 3,800 steps; the FP64 GPU state is
+# held to the oracle by the sampled tests above), both against the exact
+# solution.  Errors of the cell averages W, per component: L1 area weighted.
+@pytest.mark.parametrize("case", ["burgers200k", "vortex2m"])
+def test_fp32_full_run_against_fp64(case):
+    if case == "burgers200k":
+        mesh, eq, m, T = I.config2_mesh(), "burgers", 1, 1.5 / np.pi ** 2
+        U0 = I.initial_state(mesh, I.burgers_sine, 1)
+        exact = lambda x, y: I.burgers_exact(x, y, T)
+    else:
+        mesh, eq, m, T = I.config3_mesh(), "euler", 4, 2.0
+        U0 = I.initial_state(mesh, I.vortex, 4)
+        exact = lambda x, y: I.vortex(x, y, T)
+    area = I.cell_areas(mesh)
+    W = {}
+    for prec in ("fp64", "fp32"):
+        s = hweno.Solver(mesh, U0, eq=eq, precision=prec)
+        s.run_to(T)
+        W[prec] = s.get_state()[0][0]
+        s.close()
+    We = I.cell_averages(mesh, exact, m)
+    l1 = lambda a, b: (np.abs(a - b) * area).sum(axis=1) / area.sum()
+    d_l1, d_linf = l1(W["fp32"], W["fp64"]), np.abs(W["fp32"] - W["fp64"]).max(axis=1)
+    print(f"{case} to T={T:.4f}: FP32 - FP64 L1 {d_l1} Linf {d_linf}; "
+          f"error to exact L1 FP64 {l1(W['fp64'], We)} FP32 {l1(W['fp32'], We)}")
+    assert np.all(d_l1 < 1e-5) and np.all(d_linf < 1e-4)
+    # FP32 rounding stays far below the discretisation error
+    assert np.all(d_l1 < 0.1 * l1(W["fp64"], We))
