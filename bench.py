@@ -56,8 +56,9 @@ def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
 # dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
 # it was measured on; it is reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources_sha": "885570ae281969f5",
-    "per_cell": {"recon_fp32": 571.2, "edge_fp32": 403.6},   # 499,942-cell capture, scaled per cell
+    "sources_sha": "252397b8f4b4d22f",
+    # full-size (1,999,928-cell) single-pass ncu capture, per cell
+    "per_cell": {"recon_fp32": 635.3, "edge_fp32": 438.7, "recon_fp64": 1278.2, "edge_fp64": 876.0},
 }
 
 
