@@ -62,6 +62,17 @@ TRAFFIC = {
 }
 
 
+# Floating-point operations per cell and launch (FMA counted as 2), from the
+# executed-instruction counters of one ncu capture of the 499,942-cell vortex
+# (smsp__sass_thread_inst_executed_op_{d,f}{fma,add,mul}_pred_on.sum / cells),
+# valid for the sources hash of TRAFFIC.
+FLOPS = {"recon_fp64": 4382, "edge_fp64": 2932, "recon_fp32": 3986, "edge_fp32": 2573}
+
+# FP64 FMA throughput of this B300 per SM clock: the ALU probe
+# (paper_2607_10809_b300/probes/alu_peaks.cu) measured 1.132 TFLOP/s at 1935 MHz.
+FP64_FLOP_PER_CLOCK = 1.132e12 / 1935e6
+
+
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     for f in ("kernels.cu", "kernels.h", "device.cuh", "tma.cuh", "internal.h"):
@@ -203,6 +214,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     B.build()
     hweno.load()
+    if args.only in ("adjoint", "batched"):   # one leg alone (profiling runs)
+        leg = adjoint_leg(args) if args.only == "adjoint" else batched_leg(args, world)
+        if rank == 0:
+            print(json.dumps({"partial_run": True, args.only: leg}), flush=True)
+        return
     mesh, U0 = workload(args.workload)
     N = mesh.nt
     hmesh = hweno.Mesh(mesh)
@@ -303,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": r32["clocks"],
         "fp64": {"value": replicas_value(N, r64["K"], r64["ms"], world), "steps": r64["K"],
                  "ms_per_step": r64["ms"] / r64["K"], "kernel_ms": {"k_recon": rec64, "k_edge": edge64},
-                 "clocks": r64["clocks"]},
+                 "clocks": r64["clocks"], "roofline": fp64_roofline(N, rec64, edge64, r64["clocks"], sha)},
         "status_flags": {"fp32": r32["flags"], "fp64": r64["flags"]},
     }
     if not args.no_batch:
@@ -317,6 +333,19 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def fp64_roofline(N, rec_ms, edge_ms, clocks, sha):
+    """The FP64 form is bound by the FP64 pipe: achieved FLOP/s of its dominant
+    kernel against the probe's FP64 rate at the sampled SM clock."""
+    if TRAFFIC["sources_sha"] != sha:
+        return None
+    dom, ms = ("recon", rec_ms) if rec_ms >= edge_ms else ("edge", edge_ms)
+    achieved = FLOPS[f"{dom}_fp64"] * N / (ms * 1e-3) / 1e12
+    peak = FP64_FLOP_PER_CLOCK * clocks["sm_mhz"] * 1e6 / 1e12 if clocks.get("sm_mhz") else None
+    return {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "flop_per_cell": FLOPS[f"{dom}_fp64"],
+            "peak_kind": "FP64 FMA probe scaled to the sampled SM clock"}
+
+
 # ---------------------------------------------------------------- batched leg
 def batched_leg(args, world):
     """256 four-quadrant Riemann solves (2k-40k triangles each, FP32, scale
@@ -326,7 +355,7 @@ def batched_leg(args, world):
     import torch
     from paper_2607_10809_b300 import hweno
     meshes, states = I.config4_batch(args.batch_solves)
-    T = 0.25
+    T = args.batch_T
     b = hweno.Batch(meshes, states, eq="euler", precision="fp32", positivity=True)
     best = b.autotune(trial_steps=6)
     b.reset()
@@ -358,7 +387,7 @@ def batched_leg(args, world):
         seq_cells += n * mesh.nt
         s.close()
     return {"workload": f"{len(meshes)} four-quadrant Riemann solves on [0,1]^2, "
-                        f"{sum(m.nt for m in meshes)} triangles, FP32 + scale limiter, T=0.25",
+                        f"{sum(m.nt for m in meshes)} triangles, FP32 + scale limiter, T={T}",
             "value": cell_steps / el, "unit": UNIT, "seconds": el, "cell_steps": int(cell_steps),
             "steps_min_max": [int(min(steps)), int(max(steps))], "failed_solves": failed, "status": status,
             "schedule": best, "single_solve_sequential_value": seq_cells / seq_time,
@@ -478,9 +507,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (many solves) leg")
     ap.add_argument("--batch-solves", type=int, default=256)
+    ap.add_argument("--batch-T", type=float, default=0.25, help="final time of the batched solves")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
     ap.add_argument("--adj-steps", type=int, default=200)
-    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64"], help="precisions to run")
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "adjoint", "batched"],
+                    help="precisions to run, or one leg alone")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-cells", type=int, default=4000)
     args = ap.parse_args()
