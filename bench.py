@@ -44,12 +44,13 @@ UNIT = "tri-updates/s"
 #   k_recon reads the cell state 3m words, the reconstruction geometry 76 words
 #   and 3 neighbour indices; writes the edge-point buffer 6 * 3 * m words.
 #   k_edge reads the edge-point buffer 6 * 3 * m words, the cell averages m
-#   words, 10 geometry words and 4 index words; writes the state 3m words.
+#   words, 10 geometry words and 4 index words; writes the state 3m words; in
+#   FP32 it also reads and writes the m compensation words of the averages.
 # Neighbour data are counted once (perfect reuse through the caches).
 def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
     if kernel == "recon":
         return (3 * m + 76 + 18 * m) * s + 3 * 4
-    return (18 * m + m + 10 + 3 * m) * s + 4 * 4
+    return (18 * m + m + 10 + 3 * m) * s + 4 * 4 + (2 * m * 4 if s == 4 else 0)
 
 
 # DRAM traffic per cell (bytes) measured with ncu (dram__bytes_read.sum +

@@ -103,7 +103,11 @@ hw_status hw_mesh_neighbors(const hw_mesh* mesh, int32_t* nbr, int32_t* nbe);
 hw_status hw_mesh_permutation(const hw_mesh* mesh, int32_t* perm);
 
 /* Bytes of device workspace hw_state_init needs for this mesh / options /
- * precision (geometry, two state buffers, edge-point buffer, staging). */
+ * precision (geometry, two state buffers, edge-point buffer, staging; in
+ * HW_FP32 also one compensation word per cell and component: the FP32 form
+ * adds each step's update to the cell averages by compensated summation, so
+ * that their FP32 rounding does not accumulate over the steps; the
+ * reconstruction and the fluxes use the FP32 averages). */
 hw_status hw_workspace_bytes(const hw_mesh* mesh, const hw_options* opt, int32_t precision, size_t* bytes);
 
 /* Upload geometry and the initial state (host arrays as described above) into
@@ -127,7 +131,8 @@ hw_status hw_step(hw_solver* s, double dt);
  * non-finite / non-physical. */
 hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps);
 /* Copy the state back to host arrays in the caller's numbering and report the
- * time; synchronises.  Any pointer may be NULL to skip it. */
+ * time; synchronises.  Any pointer may be NULL to skip it.  HW_FP32: Wbar is
+ * the FP32 cell average plus its compensation, summed in double. */
 hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, double* t);
 /* Sum over cells of |K| * Wbar_K per component, accumulated in FP64 on the
  * device in a fixed order (deterministic); sums[c], synchronises. */
@@ -175,7 +180,8 @@ hw_status hw_step_static_scratch(hw_solver* s, double dt);
 hw_status hw_state_bytes(const hw_solver* s, size_t* bytes);
 /* Copy the current state to / from an internal buffer (device to device,
  * asynchronous on the stream).  Import also sets the time to t and recomputes
- * the CFL step. */
+ * the CFL step.  The FP32 compensation words are not part of the buffer:
+ * import (like hw_set_state) starts them at zero. */
 hw_status hw_state_export(hw_solver* s, void* dst);
 hw_status hw_state_import(hw_solver* s, const void* src, double t);
 /* Convert host arrays (caller numbering, double, as for hw_get_state) to an

@@ -34,7 +34,7 @@ constexpr int kGraphSteps = 16;  // steps per captured graph (even: the state pa
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t rgeo, igeo, U0, U1, Pb, area, perm, stage, sc, partial, consv, total;
+  size_t rgeo, igeo, U0, U1, Pb, comp, comp_bytes, area, perm, stage, sc, partial, consv, total;
 };
 
 Layout make_layout(int64_t N, int m, int prec) {
@@ -48,6 +48,9 @@ Layout make_layout(int64_t N, int m, int prec) {
   L.U0 = take((size_t)3 * m * ld * s);
   L.U1 = take((size_t)3 * m * ld * s);
   L.Pb = take((size_t)18 * m * ld * s);
+  // FP32 form: compensation of the cell averages (compensated summation of the updates)
+  L.comp_bytes = prec == HW_FP32 ? (size_t)m * ld * 4 : 0;
+  L.comp = take(L.comp_bytes);
   L.area = take((size_t)N * 8);
   L.perm = take((size_t)N * 4);
   L.stage = take((size_t)3 * m * N * 8);
@@ -135,6 +138,11 @@ struct hw_solver {
 
   void* U(int k) { return ws + (k == 0 ? L.U0 : L.U1); }
   DevScalars* sc() { return reinterpret_cast<DevScalars*>(ws + L.sc); }
+  void* comp() { return L.comp_bytes ? ws + L.comp : nullptr; }
+  hw_status clear_comp() {
+    if (L.comp_bytes) HW_CUDA(cudaMemsetAsync(ws + L.comp, 0, L.comp_bytes, stream));
+    return HW_OK;
+  }
   StepArgs args(int from, double dt_fixed) {
     StepArgs a{};
     a.rgeo = ws + L.rgeo;
@@ -147,6 +155,7 @@ struct hw_solver {
     a.U = U(from);
     a.Un = U(1 - from);
     a.Pb = ws + L.Pb;
+    a.C = comp();
     a.sc = sc();
     a.dt_fixed = dt_fixed;
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
@@ -224,6 +233,7 @@ static hw_status upload_state(hw_solver* s, const double* W, const double* V, co
   HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + 2 * plane, Y, plane, cudaMemcpyHostToDevice, s->stream));
   launch_scatter(s->prec, stage, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld,
                  3 * s->m, s->U(s->cur), s->stream);
+  if (hw_status st = s->clear_comp()) return st;
   launch_reset(s->sc(), t, s->opt.cfl, s->stream);
   launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
   HW_CUDA(cudaGetLastError());
@@ -359,8 +369,8 @@ hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, d
   if (!s) return fail(HW_EINVAL, "null solver");
   const size_t plane = (size_t)s->m * s->N * sizeof(double);
   double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
-  launch_gather(s->prec, s->U(s->cur), reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld,
-                3 * s->m, stage, s->stream);
+  launch_gather(s->prec, s->U(s->cur), s->comp(), s->m, reinterpret_cast<const int32_t*>(s->ws + s->L.perm),
+                (int)s->N, (int)s->ld, 3 * s->m, stage, s->stream);
   HW_CUDA(cudaGetLastError());
   if (Wbar) HW_CUDA(cudaMemcpyAsync(Wbar, stage, plane, cudaMemcpyDeviceToHost, s->stream));
   if (Vbar) HW_CUDA(cudaMemcpyAsync(Vbar, reinterpret_cast<char*>(stage) + plane, plane, cudaMemcpyDeviceToHost, s->stream));
@@ -375,8 +385,8 @@ hw_status hw_conservation(hw_solver* s, double* sums) {
   if (!s || !sums) return fail(HW_EINVAL, "null pointer");
   double* partial = reinterpret_cast<double*>(s->ws + s->L.partial);
   double* out = reinterpret_cast<double*>(s->ws + s->L.consv);
-  launch_consv(s->prec, s->U(s->cur), reinterpret_cast<const double*>(s->ws + s->L.area), (int)s->N, (int)s->ld,
-               s->m, partial, out, s->stream);
+  launch_consv(s->prec, s->U(s->cur), s->comp(), reinterpret_cast<const double*>(s->ws + s->L.area), (int)s->N,
+               (int)s->ld, s->m, partial, out, s->stream);
   HW_CUDA(cudaGetLastError());
   HW_CUDA(cudaMemcpyAsync(s->h_consv, out, s->m * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   HW_CUDA(cudaStreamSynchronize(s->stream));
@@ -539,6 +549,7 @@ hw_status hw_state_export(hw_solver* s, void* dst) {
 hw_status hw_state_import(hw_solver* s, const void* src, double t) {
   if (!s || !src) return fail(HW_EINVAL, "null pointer");
   HW_CUDA(cudaMemcpyAsync(s->U(s->cur), src, state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+  if (hw_status st = s->clear_comp()) return st;
   launch_reset(s->sc(), t, s->opt.cfl, s->stream);
   launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
   HW_CUDA(cudaGetLastError());
@@ -563,8 +574,8 @@ hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, doubl
   if (!s || !src) return fail(HW_EINVAL, "null pointer");
   const size_t plane = (size_t)s->m * s->N * sizeof(double);
   double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
-  launch_gather(s->prec, src, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld, 3 * s->m,
-                stage, s->stream);
+  launch_gather(s->prec, src, nullptr, s->m, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N,
+                (int)s->ld, 3 * s->m, stage, s->stream);
   HW_CUDA(cudaGetLastError());
   if (Wbar) HW_CUDA(cudaMemcpyAsync(Wbar, stage, plane, cudaMemcpyDeviceToHost, s->stream));
   if (Vbar) HW_CUDA(cudaMemcpyAsync(Vbar, reinterpret_cast<char*>(stage) + plane, plane, cudaMemcpyDeviceToHost, s->stream));

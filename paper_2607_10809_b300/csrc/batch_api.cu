@@ -442,7 +442,8 @@ hw_status hw_batch_get_state(hw_batch* b, int32_t solve, double* Wbar, double* V
   const size_t nt = (size_t)b->plan.nt[solve], off = (size_t)b->plan.off[solve];
   const char* U = b->ws + ((x.nsteps & 1) ? b->L.U1 : b->L.U0) + off * 3 * m * es;
   double* stage = reinterpret_cast<double*>(b->ws + b->L.stage);
-  launch_gather(b->prec, U, reinterpret_cast<const int32_t*>(b->ws + b->L.perm) + off, (int)nt, 0, (int)(3 * m),
+  launch_gather(b->prec, U, nullptr, (int)m, reinterpret_cast<const int32_t*>(b->ws + b->L.perm) + off, (int)nt, 0,
+                (int)(3 * m),
                 stage, b->stream);
   HB_CUDA(cudaGetLastError());
   const size_t plane = m * nt * 8;

@@ -130,6 +130,8 @@ template <typename R> struct SingleCtx {
   double dt;
   DevScalars* sc;
   double local_min;   // CFL minimum of this thread over its tiles
+  R* C;               // compensation of the cell averages (FP32 form) or nullptr
+  __device__ __forceinline__ R* comp(int) const { return C; }
   __device__ __forceinline__ int ntiles() const { return ts.ntiles; }
   __device__ __forceinline__ bool active(int) const { return true; }
   __device__ __forceinline__ void range(int tile, int& c0, int& cnt) const { tile_range(ts, N, tile, c0, cnt); }
@@ -145,6 +147,7 @@ template <typename R> struct SingleCtx {
 template <typename R> struct BatchCtx {
   const int4* tiles;   // (first cell, count, solve, 0)
   int nt;
+  __device__ __forceinline__ R* comp(int) const { return nullptr; }   // batched solves: plain updates
   BatchSolve* bs;
   BatchCtl* ctl;
   R* U0;
@@ -500,13 +503,17 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
             for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
           }
         }
-        // Gauss weight 1/2 and the cell's outward normal (+-n)
+        // Gauss weight 1/2 and the cell's outward normal (+-n).  In FP32 the
+        // Green-Gauss terms are taken relative to the cell's own average: the
+        // cell's |e| n sum to zero, so the result is the same, while the terms
+        // shrink from |W| / h to |grad W| and their rounding with them.
         const R sgn = left ? R(0.5) * el : R(-0.5) * el;
 #pragma unroll
         for (int c = 0; c < m; ++c) {
+          const R sh = sizeof(R) == 4 ? Sh[c] - Wi[c] : Sh[c];
           part[0][c][qp][lc] = sgn * Fe[c];
-          part[1][c][qp][lc] = sgn * nx * Sh[c];
-          part[2][c][qp][lc] = sgn * ny * Sh[c];
+          part[1][c][qp][lc] = sgn * nx * sh;
+          part[2][c][qp][lc] = sgn * ny * sh;
         }
       }
     }
@@ -521,7 +528,19 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
         for (int qp = 0; qp < 6; ++qp) r += part[kind][c][qp][lc];
         R v = r;
         if (kind == 0) {
-          v = S.u[lc][c] - dtr * r;
+          R* Cp = ctx.comp(tile);
+          if (Cp) {
+            // compensated summation of the updates: the rounding error of each
+            // new average is carried into the next update, so that the FP32
+            // averages do not accumulate one rounding per step
+            R& cc = Cp[(size_t)(cell0 + lc) * m + c];
+            const R y = -dtr * r - cc;
+            const R w = S.u[lc][c];
+            v = w + y;
+            cc = (v - w) - y;
+          } else {
+            v = S.u[lc][c] - dtr * r;
+          }
           wn[c][lc] = v;
         }
         Un[(size_t)(cell0 + lc) * 3 * m + o] = v;
@@ -560,7 +579,7 @@ __global__ void __launch_bounds__(LIM ? kThreads : kLeanThreads) k_recon(const _
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + recon_smem_bytes<R, EQ>() - 128 - 2 * sizeof(uint64_t));
   const volatile DevScalars* vsc = sc;
   if (vsc->done) return;
-  SingleCtx<R> ctx{ts, G.N, U, nullptr, dt_fixed > 0 ? dt_fixed : vsc->dt, sc, dinf()};
+  SingleCtx<R> ctx{ts, G.N, U, nullptr, dt_fixed > 0 ? dt_fixed : vsc->dt, sc, dinf(), nullptr};
   if (threadIdx.x == 0) {
     prefetch_tensormap(&mGeo); prefetch_tensormap(&mIdx);
     mbar_init(&bar[0], 1);
@@ -576,7 +595,7 @@ template <typename R, int EQ>
 __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUtensorMap mEgeo,
                                                     const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
                                                     const R* __restrict__ U, R* __restrict__ Un,
-                                                    const R* __restrict__ Pb, EqParams P, DevScalars* sc,
+                                                    const R* __restrict__ Pb, R* C, EqParams P, DevScalars* sc,
                                                     double dt_fixed, TileSet ts) {
   constexpr int m = EqTraits<EQ>::m;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -594,7 +613,7 @@ __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUten
     return;
   }
   const double dt = dt_fixed > 0 ? dt_fixed : vs->dt;
-  SingleCtx<R> ctx{ts, N, U, Un, dt, sc, dinf()};
+  SingleCtx<R> ctx{ts, N, U, Un, dt, sc, dinf(), C};
   if (t == 0) {
     prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
     mbar_init(&bar[0], 1);
@@ -732,13 +751,14 @@ __global__ void __launch_bounds__(256) k_cfl(GeoView<R> G, const R* __restrict__
 
 // Deterministic FP64 sums of |K| Wbar_K: fixed grid, fixed tree, then one block.
 template <typename R>
-__global__ void __launch_bounds__(256) k_consv_partial(const R* __restrict__ U, const double* __restrict__ area, int N,
-                                                        int ld, int m, double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_consv_partial(const R* __restrict__ U, const R* __restrict__ C,
+                                                        const double* __restrict__ area, int N, int ld, int m,
+                                                        double* __restrict__ partial) {
   __shared__ double sh[256];
   for (int c = 0; c < m; ++c) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-      s += area[i] * (double)U[(size_t)i * 3 * m + c];
+      s += area[i] * ((double)U[(size_t)i * 3 * m + c] + (C ? (double)C[(size_t)i * m + c] : 0.0));
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -769,12 +789,17 @@ __global__ void k_scatter_state(const double* __restrict__ host_order, const int
   for (int k = 0; k < planes; ++k) U[(size_t)i * planes + k] = (R)host_order[(size_t)k * N + src];
 }
 template <typename R>
-__global__ void k_gather_state(const R* __restrict__ U, const int32_t* __restrict__ perm, int N, int ld, int planes,
+__global__ void k_gather_state(const R* __restrict__ U, const R* __restrict__ C, int m,
+                               const int32_t* __restrict__ perm, int N, int ld, int planes,
                                double* __restrict__ host_order) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int dst = perm[i];
-  for (int k = 0; k < planes; ++k) host_order[(size_t)k * N + dst] = (double)U[(size_t)i * planes + k];
+  for (int k = 0; k < planes; ++k) {
+    double v = (double)U[(size_t)i * planes + k];
+    if (C && k < m) v += (double)C[(size_t)i * m + k];   // the cell averages with their compensation
+    host_order[(size_t)k * N + dst] = v;
+  }
 }
 
 __global__ void k_reset(DevScalars* sc, double t, double cfl) {
@@ -906,7 +931,7 @@ template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t
   const int nt = a.tiles.ntiles;
   k_edge<R, EQ><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
       a.maps->egeo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
-      reinterpret_cast<const R*>(a.Pb), a.P, a.sc, a.dt_fixed, a.tiles);
+      reinterpret_cast<const R*>(a.Pb), reinterpret_cast<R*>(a.C), a.P, a.sc, a.dt_fixed, a.tiles);
 }
 template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
@@ -942,12 +967,14 @@ void launch_set_target(DevScalars* sc, double T, int has_T, cudaStream_t st) {
   k_set_target<<<1, 32, 0, st>>>(sc, T, has_T);
 }
 
-void launch_consv(int prec, const void* U, const double* area, int N, int ld, int m, double* partial, double* out,
-                  cudaStream_t st) {
+void launch_consv(int prec, const void* U, const void* C, const double* area, int N, int ld, int m, double* partial,
+                  double* out, cudaStream_t st) {
   if (prec == 0)
-    k_consv_partial<double><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const double*>(U), area, N, ld, m, partial);
+    k_consv_partial<double><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const double*>(U),
+                                                          reinterpret_cast<const double*>(C), area, N, ld, m, partial);
   else
-    k_consv_partial<float><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const float*>(U), area, N, ld, m, partial);
+    k_consv_partial<float><<<kConsvBlocks, 256, 0, st>>>(reinterpret_cast<const float*>(U),
+                                                         reinterpret_cast<const float*>(C), area, N, ld, m, partial);
   k_consv_final<<<1, 32, 0, st>>>(partial, kConsvBlocks, m, out);
 }
 
@@ -1029,13 +1056,15 @@ void launch_batch_dt(BatchSolve* bs, int n, double cfl, double T, int has_T, cud
 
 void launch_batch_reset_ctl(BatchCtl* ctl, cudaStream_t st) { k_batch_reset_ctl<<<1, 32, 0, st>>>(ctl); }
 
-void launch_gather(int prec, const void* U, const int32_t* perm, int N, int ld, int planes, double* host_order,
-                   cudaStream_t st) {
+void launch_gather(int prec, const void* U, const void* C, int m, const int32_t* perm, int N, int ld, int planes,
+                   double* host_order, cudaStream_t st) {
   const int nb = (N + 255) / 256;
   if (prec == 0)
-    k_gather_state<double><<<nb, 256, 0, st>>>(reinterpret_cast<const double*>(U), perm, N, ld, planes, host_order);
+    k_gather_state<double><<<nb, 256, 0, st>>>(reinterpret_cast<const double*>(U), reinterpret_cast<const double*>(C),
+                                               m, perm, N, ld, planes, host_order);
   else
-    k_gather_state<float><<<nb, 256, 0, st>>>(reinterpret_cast<const float*>(U), perm, N, ld, planes, host_order);
+    k_gather_state<float><<<nb, 256, 0, st>>>(reinterpret_cast<const float*>(U), reinterpret_cast<const float*>(C), m,
+                                              perm, N, ld, planes, host_order);
 }
 
 }  // namespace hw

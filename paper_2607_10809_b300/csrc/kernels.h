@@ -65,6 +65,8 @@ struct StepArgs {
   const void* U;           // state in  [ld][3m] (record per cell)
   void* Un;                // state out [ld][3m]
   void* Pb;                // edge-point buffer [ld][6][3][m]
+  void* C;                 // FP32 form: compensation of the cell averages [ld][m] (compensated
+                           // summation of the updates), updated in place; nullptr: none
   const TensorMaps* maps;
   TileSet tiles;
   DevScalars* sc;
@@ -128,12 +130,12 @@ void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st);
 void launch_set_target(DevScalars* sc, double T, int has_T, cudaStream_t st);
-void launch_consv(int prec, const void* U, const double* area, int N, int ld, int m, double* partial, double* out,
-                  cudaStream_t st);
+void launch_consv(int prec, const void* U, const void* C, const double* area, int N, int ld, int m, double* partial,
+                  double* out, cudaStream_t st);
 void launch_scatter(int prec, const double* host_order, const int32_t* perm, int N, int ld, int planes, void* U,
                     cudaStream_t st);
-void launch_gather(int prec, const void* U, const int32_t* perm, int N, int ld, int planes, double* host_order,
-                   cudaStream_t st);
+void launch_gather(int prec, const void* U, const void* C, int m, const int32_t* perm, int N, int ld, int planes,
+                   double* host_order, cudaStream_t st);
 
 }  // namespace hw
 
