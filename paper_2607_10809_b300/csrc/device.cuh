@@ -45,6 +45,10 @@ inline void eq_params_finish(EqParams& P) {
   for (int l = 0; l < 4; ++l) P.gf[l] = (float)P.g[l];
 }
 
+// 1 / x correctly rounded (the same value as the IEEE division 1 / x)
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
 // the constants in the working precision R
 template <typename R> struct EqC {
   static __device__ __forceinline__ R ax(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.ax; else return P.axf; }
@@ -109,7 +113,7 @@ __device__ __forceinline__ void nonlinear_weights(float Wave, const float beta[4
     for (int l = 0; l < 4; ++l) om[l] = P.gf[l];
     return;
   }
-  const float is = 1.0f / s;
+  const float is = recip(s);
 #pragma unroll
   for (int l = 0; l < 4; ++l) om[l] = wb[l] * is;
 }
@@ -200,7 +204,7 @@ template <typename R> __device__ __forceinline__ Jet<R> jmul(const Jet<R>& a, co
 }
 template <typename R> __device__ __forceinline__ Jet<R> jrecip(const Jet<R>& a) {
   Jet<R> r;
-  r.v = R(1) / a.v;
+  r.v = recip(a.v);
   const R r2 = r.v * r.v;
   r.x = -a.x * r2;
   r.y = -a.y * r2;
@@ -271,7 +275,7 @@ __device__ __forceinline__ void flux_n(const R* W, R nx, R ny, const EqParams& P
   } else if constexpr (EQ == kEqBurgers) {
     H[0] = R(0.5) * W[0] * W[0] * (nx + ny);
   } else {
-    const R ir = R(1) / W[0];
+    const R ir = recip(W[0]);
     const R u = W[1] * ir, v = W[2] * ir;
     const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
     const R un = u * nx + v * ny;
@@ -290,7 +294,7 @@ __device__ __forceinline__ R spectral_radius_n(const R* W, R nx, R ny, const EqP
   } else if constexpr (EQ == kEqBurgers) {
     return fabs(W[0] * (nx + ny));
   } else {
-    const R ir = R(1) / W[0];
+    const R ir = recip(W[0]);
     const R u = W[1] * ir, v = W[2] * ir;
     const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
     return fabs(u * nx + v * ny) + sqrt(EqC<R>::gam(P) * p * ir);
@@ -306,7 +310,7 @@ __device__ __forceinline__ R spectral_radius_all(const R* W, const EqParams& P) 
   } else if constexpr (EQ == kEqBurgers) {
     return R(1.4142135623730951) * fabs(W[0]);
   } else {
-    const R ir = R(1) / W[0];
+    const R ir = recip(W[0]);
     const R u = W[1] * ir, v = W[2] * ir;
     const R p = EqC<R>::gm1(P) * (W[3] - R(0.5) * (W[1] * u + W[2] * v));
     return sqrt(u * u + v * v) + sqrt(EqC<R>::gam(P) * p * ir);

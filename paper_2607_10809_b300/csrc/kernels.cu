@@ -389,7 +389,12 @@ template <typename R, int EQ> struct EdgeStage {
   int32_t idx[4][kCells];        // TMA tensor box
   R pb[kCells][18 * m];          // bulk copy of the tile's edge-point records
   R u[kCells][3 * m];            // bulk copy of the tile's state records
+  R cc[kCells][m];               // bulk copy of the compensation words (FP32 form; else unused)
 };
+
+static_assert(sizeof(EdgeStage<float, 2>) % 128 == 0 && sizeof(EdgeStage<double, 2>) % 128 == 0 &&
+                  sizeof(EdgeStage<float, 0>) % 128 == 0 && sizeof(EdgeStage<double, 0>) % 128 == 0,
+              "every stage starts 128-byte aligned (TMA destination)");
 
 template <typename R, int EQ> constexpr size_t edge_smem_bytes() {
   return 2 * sizeof(EdgeStage<R, EQ>) + sizeof(R) * 3 * EqTraits<EQ>::m * 6 * kCells +
@@ -413,11 +418,13 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
   auto issue = [&](int s, int tile) {
     int c0, cnt;
     ctx.range(tile, c0, cnt);
-    mbar_arrive_expect_tx(&bar[s], kBytes);
+    const R* C = ctx.comp(tile);
+    mbar_arrive_expect_tx(&bar[s], C ? kBytes : kBytes - (unsigned)sizeof(Stage::cc));
     tma_load_2d(&st[s].geo[0][0], mEgeo, c0, 0, &bar[s]);
     tma_load_2d(&st[s].idx[0][0], mIdx, c0, 0, &bar[s]);
     bulk_load(&st[s].pb[0][0], Pb + (size_t)c0 * 18 * m, kCells * 18 * m * sizeof(R), &bar[s]);
     bulk_load(&st[s].u[0][0], ctx.uin(tile) + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+    if (C) bulk_load(&st[s].cc[0][0], C + (size_t)c0 * m, kCells * m * sizeof(R), &bar[s]);
   };
   int tile = next_active(ctx, blockIdx.x);
   if (t == 0 && tile < ntiles) {
@@ -533,11 +540,10 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
             // compensated summation of the updates: the rounding error of each
             // new average is carried into the next update, so that the FP32
             // averages do not accumulate one rounding per step
-            R& cc = Cp[(size_t)(cell0 + lc) * m + c];
-            const R y = -dtr * r - cc;
+            const R y = -dtr * r - S.cc[lc][c];
             const R w = S.u[lc][c];
             v = w + y;
-            cc = (v - w) - y;
+            Cp[(size_t)(cell0 + lc) * m + c] = (v - w) - y;
           } else {
             v = S.u[lc][c] - dtr * r;
           }
