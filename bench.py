@@ -75,10 +75,14 @@ FP64_FLOP_PER_CLOCK = 1.132e12 / 1935e6
 
 
 def kernel_sources_sha() -> str:
+    """Hash of the step kernels' code (comments and blank space ignored)."""
+    import re
     h = hashlib.sha256()
     for f in ("kernels.cu", "kernels.h", "device.cuh", "tma.cuh", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2607_10809_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2607_10809_b300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

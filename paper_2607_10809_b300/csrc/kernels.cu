@@ -10,7 +10,9 @@
 //             cells of an edge obtain bitwise-identical values; the update of
 //             the cell average (Eq. flx) and of the derivative averages by
 //             Green-Gauss from the central values at t_{n+1} (Eqs. derave2d2,
-//             timeflux, taylor2dtime); the CFL step of the next step.
+//             timeflux, taylor2dtime); the CFL step of the next step.  In
+//             FP32 the update of the average is a compensated sum (one FP32
+//             compensation word per cell and component).
 //   k_cfl, k_consv, k_scatter_state, k_gather_state: CFL step of a state,
 //             FP64 conservation sums, host-order <-> internal-order copies.
 //
@@ -19,8 +21,10 @@
 // cell) are records, one contiguous record per cell, so that a neighbour's
 // data are a few 16-byte vector loads.
 //
-// Both main kernels walk tiles of kCells consecutive (Hilbert-ordered) cells
-// with 6 threads per cell.  A block stages each tile's dense operands
+// Both main kernels walk tiles of kCells consecutive (Hilbert-ordered) cells:
+// k_recon with 2 threads per cell (the per-component and per-point tasks of a
+// tile in whole passes; 6 per cell with the scale limiter), k_edge and the
+// batched kernel with 6.  A block stages each tile's dense operands
 // (geometry planes and neighbour indices by TMA tensor loads, the tile's own
 // state or edge-point records by bulk copies) in shared memory,
 // double-buffered: the copies of the block's next tile are in flight while the
