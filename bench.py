@@ -57,9 +57,9 @@ def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
 # dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
 # it was measured on; it is reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources_sha": "252397b8f4b4d22f",
+    "sources_sha": "b2c4a99d92a51144",
     # full-size (1,999,928-cell) single-pass ncu capture, per cell
-    "per_cell": {"recon_fp32": 635.3, "edge_fp32": 438.7, "recon_fp64": 1278.2, "edge_fp64": 876.0},
+    "per_cell": {"recon_fp32": 634.3, "edge_fp32": 467.1, "recon_fp64": 1277.6, "edge_fp64": 872.5},
 }
 
 
@@ -67,7 +67,7 @@ TRAFFIC = {
 # executed-instruction counters of one ncu capture of the 499,942-cell vortex
 # (smsp__sass_thread_inst_executed_op_{d,f}{fma,add,mul}_pred_on.sum / cells),
 # valid for the sources hash of TRAFFIC.
-FLOPS = {"recon_fp64": 4382, "edge_fp64": 2932, "recon_fp32": 3986, "edge_fp32": 2573}
+FLOPS = {"recon_fp64": 4382, "edge_fp64": 2932, "recon_fp32": 3986, "edge_fp32": 2609}
 
 # FP64 FMA throughput of this B300 per SM clock: the ALU probe
 # (paper_2607_10809_b300/probes/alu_peaks.cu) measured 1.132 TFLOP/s at 1935 MHz.
@@ -257,6 +257,14 @@ def run_ours(args, rank, world, local_rank):
         s.profile(False)
         flags = s.status_flags()
         results[prec] = {"K": K, "ms": ms, "prof": prof, "clocks": clk.summary(), "flags": flags}
+        if args.only == "both":
+            # accuracy of the FP32 form against the FP64 form: the same fixed
+            # steps from the initial state (outside the timed region)
+            s.set_state(U0, 0.0)
+            dt_fix = 0.5 * s.time()[1]
+            for _ in range(args.acc_steps):
+                s.step(dt_fix)
+            results.setdefault("acc", {})[prec] = (s.get_state()[0], dt_fix)
         if prec == "fp32" and not args.no_e2e:
             # end to end through the C ABI with host buffers: H2D state, step, D2H state
             Upin = torch.empty((3, 4, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -279,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     if args.only != "both" or args.no_e2e:
-        print(json.dumps({"partial_run": True, "N": N, **{k: v for k, v in results.items()}}), flush=True)
+        print(json.dumps({"partial_run": True, "N": N, **{k: v for k, v in results.items() if k != "acc"}}), flush=True)
         return
     hbm, peak_kind = measured_peaks()
     r32 = results["fp32"]
@@ -296,6 +304,14 @@ def run_ours(args, rank, world, local_rank):
     rec64 = r64["prof"]["recon_ms"] / max(1, r64["prof"]["steps"])
     edge64 = r64["prof"]["edge_ms"] / max(1, r64["prof"]["steps"])
     e2e = results["e2e"]
+    acc = None
+    if "acc" in results and len(results["acc"]) == 2:
+        (U32, dt32), (U64, dt64) = results["acc"]["fp32"], results["acc"]["fp64"]
+        if abs(dt32 - dt64) <= 1e-6 * dt64:
+            area = I.cell_areas(mesh)
+            d = np.abs(U32[0] - U64[0])
+            acc = {"steps": args.acc_steps, "what": "cell averages, FP32 - FP64 after the same fixed steps",
+                   "l1": ((d * area).sum(axis=1) / area.sum()).tolist(), "linf": d.max(axis=1).tolist()}
     line = {
         "metric": METRIC,
         "value": value,
@@ -326,6 +342,7 @@ def run_ours(args, rank, world, local_rank):
                  "ms_per_step": r64["ms"] / r64["K"], "kernel_ms": {"k_recon": rec64, "k_edge": edge64},
                  "clocks": r64["clocks"], "roofline": fp64_roofline(N, rec64, edge64, r64["clocks"], sha)},
         "status_flags": {"fp32": r32["flags"], "fp64": r64["flags"]},
+        "fp32_vs_fp64": acc,
     }
     if not args.no_batch:
         line["batched"] = batched_leg(args, world)
@@ -356,7 +373,9 @@ def batched_leg(args, world):
     """256 four-quadrant Riemann solves (2k-40k triangles each, FP32, scale
     limiter) advanced to T = 0.25 in one persistent launch with the autotuned
     schedule, against the same solves run one after another through the
-    single-solve path."""
+    single-solve path, and against the plain FP64 single-solve form on a
+    sample of the solves (its throughput, and the batched FP32 states'
+    relative L1 difference to it, per solve that both forms carried to T)."""
     import torch
     from paper_2607_10809_b300 import hweno
     meshes, states = I.config4_batch(args.batch_solves)
@@ -376,6 +395,11 @@ def batched_leg(args, world):
     el = time.perf_counter() - t0
     failed = sum(1 for k in range(len(meshes)) if b.get_state(k)[3])
     steps = [b.get_state(k)[2] for k in range(len(meshes))]
+    # a sample of the solves (spread over the sizes) for the FP64 reference below
+    nref = min(args.batch_fp64_solves, len(meshes))
+    order = np.argsort([m.nt for m in meshes], kind="stable")
+    sample = [int(order[int(round(k * (len(meshes) - 1) / max(1, nref - 1)))]) for k in range(nref)]
+    batched_states = {k: b.get_state(k) for k in sample}
     b.close()
     # the same solves one by one through the single-solve path (graph-captured run_to)
     seq_cells, seq_time = 0, 0.0
@@ -391,12 +415,38 @@ def batched_leg(args, world):
         seq_time += time.perf_counter() - t1
         seq_cells += n * mesh.nt
         s.close()
+    # the plain FP64 single-solve form on the sample: its throughput, and the
+    # batched FP32 states against it
+    ref_cells, ref_time, errs = 0, 0.0, []
+    for k in sample:
+        s = hweno.Solver(meshes[k], states[k], eq="euler", precision="fp64", positivity=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        try:
+            n = s.run_to(T)
+            ok = True
+        except hweno.HwError:
+            n, ok = s.time()[2], False
+        torch.cuda.synchronize()
+        ref_time += time.perf_counter() - t1
+        ref_cells += n * meshes[k].nt
+        Ub, tb, _, fb = batched_states[k]
+        if ok and not fb:
+            U64 = s.get_state()[0]
+            area = I.cell_areas(meshes[k])
+            d = np.abs(Ub[0] - U64[0])
+            errs.append(float(((d * area).sum(axis=1) / area.sum() / np.abs(U64[0]).max(axis=1)).max()))
+        s.close()
+    fp64_ref = {"solves": sample, "value": ref_cells / ref_time, "unit": UNIT, "seconds": ref_time,
+                "fp32_batched_vs_fp64_rel_l1": {"median": float(np.median(errs)) if errs else None,
+                                                 "max": float(np.max(errs)) if errs else None,
+                                                 "solves_compared": len(errs)}}
     return {"workload": f"{len(meshes)} four-quadrant Riemann solves on [0,1]^2, "
                         f"{sum(m.nt for m in meshes)} triangles, FP32 + scale limiter, T={T}",
             "value": cell_steps / el, "unit": UNIT, "seconds": el, "cell_steps": int(cell_steps),
             "steps_min_max": [int(min(steps)), int(max(steps))], "failed_solves": failed, "status": status,
             "schedule": best, "single_solve_sequential_value": seq_cells / seq_time,
-            "single_solve_sequential_seconds": seq_time}
+            "single_solve_sequential_seconds": seq_time, "fp64_single_solve": fp64_ref}
 
 
 # ---------------------------------------------------------------- adjoint leg
@@ -518,6 +568,9 @@ def main():
     ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "adjoint", "batched"],
                     help="precisions to run, or one leg alone")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--acc-steps", type=int, default=50, help="fixed steps of the FP32-vs-FP64 accuracy check")
+    ap.add_argument("--batch-fp64-solves", type=int, default=16,
+                    help="solves of the batch re-run one by one in FP64 (accuracy and FP64 throughput)")
     ap.add_argument("--ref-cells", type=int, default=4000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
