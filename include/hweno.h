@@ -89,7 +89,13 @@ void hw_options_default(hw_options* opt);
  *   Lx,Ly: period in x / y (0 = not periodic); a periodic mesh lists each
  *          vertex once and triangles refer to vertices modulo the period
  *   bc   : hw_bc; HW_BC_PERIODIC requires every edge to have two triangles
- * Errors: HW_EINVAL (null pointers, indices out of range), HW_EMESH. */
+ * Sizes: 1 <= ntri <= 2^30 - 1; in practice the device workspace bounds it
+ * (hw_workspace_bytes: about 745 bytes per triangle for FP32 Euler).
+ * Errors: HW_EINVAL (null pointers, an empty mesh, ntri beyond 2^30 - 1,
+ * indices out of range, a periodic mesh without positive periods), HW_EMESH
+ * (degenerate or clockwise triangle, an edge shared by more than two
+ * triangles, an open edge on a periodic mesh, a mesh too coarse for its
+ * period, an ill-conditioned stencil; hw_last_error names which). */
 hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, int64_t ntri, double Lx, double Ly,
                          int32_t bc, hw_mesh** out);
 hw_status hw_mesh_destroy(hw_mesh* mesh);

@@ -1,6 +1,7 @@
 """Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
 declared symbol, and its FP64 mesh precompute matches the oracle bit for bit
 on connectivity."""
+import ctypes
 import os
 import re
 
@@ -101,3 +102,26 @@ def test_workspace_grows_with_mesh_and_precision(lib):
     assert wb64 > 3.5 * wa64 and wb32 < wb64
     with pytest.raises(hweno.HwError):
         hweno.hw_workspace_bytes(a.h, hweno.options("euler", cfl=-1.0), "fp64")
+
+
+def test_empty_and_degenerate_inputs_are_rejected(lib):
+    """Empty meshes and batches, and a triangle of zero area, are refused on
+    the host with their status (no device work is attempted)."""
+    L = hweno.load()
+    h = ctypes.c_void_p()
+    xy = np.zeros((3, 2)); tri = np.zeros((0, 3), np.int32)
+    rc = L.hw_mesh_create(xy.ctypes.data_as(ctypes.c_void_p), 3, tri.ctypes.data_as(ctypes.c_void_p), 0,
+                          1.0, 1.0, 1, ctypes.byref(h))
+    assert rc == hweno.HW_EINVAL and b"empty" in L.hw_last_error()
+    # collinear vertices: zero area
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [2.0, 0.0], [0.0, 1.0]])
+    tri = np.array([[0, 1, 2], [0, 1, 3]], np.int32)
+    rc = L.hw_mesh_create(xy.ctypes.data_as(ctypes.c_void_p), 4, tri.ctypes.data_as(ctypes.c_void_p), 2,
+                          0.0, 0.0, 1, ctypes.byref(h))
+    assert rc == hweno.HW_EMESH and b"degenerate" in L.hw_last_error()
+    o = hweno.options("euler")
+    n = ctypes.c_size_t()
+    assert L.hw_batch_workspace_bytes(None, 0, ctypes.byref(o), 1, ctypes.byref(n)) == hweno.HW_EINVAL
+    b = ctypes.c_void_p()
+    rc = L.hw_batch_create(None, 0, ctypes.byref(o), 1, None, None, None, None, 0, None, ctypes.byref(b))
+    assert rc == hweno.HW_EINVAL and b"empty" in L.hw_last_error()
