@@ -69,6 +69,14 @@ typedef struct {
                            pulled toward the cell average so that density and
                            pressure stay >= min(1e-13, rho_bar, p_bar) at the six
                            edge Gauss points and the three time nodes; 0 = off */
+  int32_t time_rule;    /* time quadrature of the edge flux (Eq. flux): 0 = three-node
+                           Gauss-Lobatto (Simpson) whose t_{n+1} node also gives the
+                           Green-Gauss central values (Section 2.3, default); 1 = two-node
+                           Gauss-Legendre, with the central values from a separate Taylor
+                           evaluation at t_{n+1}.  1 is for the single-solve step only: it
+                           is refused with the scale limiter, by the batched form and by
+                           the adjoint step (HW_EINVAL) */
+  int32_t reserved;     /* 0 */
   double ax, ay;        /* advection velocity (HW_ADVECTION) */
   double gamma_gas;     /* ratio of specific heats (HW_EULER) */
   double cfl;           /* dt = cfl * min_K inradius_K / lambda_K */

@@ -45,6 +45,7 @@ def lib():
                                     ctypes.c_int, P(vp)]
         _lib.orc_destroy.argtypes = [vp]
         _lib.orc_set_positivity.argtypes = [vp, ctypes.c_int]
+        _lib.orc_set_time_rule.argtypes = [vp, ctypes.c_int]
         _lib.orc_neighbors.argtypes = [vp, vp, vp]
         _lib.orc_cell_geometry.argtypes = [vp, vp]
         _lib.orc_cfl_dt.argtypes = [vp, vp]
@@ -74,7 +75,7 @@ class Oracle:
 
     def __init__(self, mesh, eq: str = "advection", a=(1.0, 1.0), gamma_gas: float = 1.4, cfl: float = 0.5,
                  gamma_lin=(0.94, 0.02, 0.02, 0.02), eps: float = 1e-8, linear_only: bool = False,
-                 positivity: bool = False):
+                 positivity: bool = False, time_rule: str = "lobatto"):
         L = lib()
         self.mesh = mesh
         self.eq = EQ[eq]
@@ -90,6 +91,8 @@ class Oracle:
         self._h = h
         if positivity:
             _check(L.orc_set_positivity(h, 1))
+        if time_rule != "lobatto":
+            _check(L.orc_set_time_rule(h, {"gauss": 1}[time_rule]))
         self.a = a
         self.gamma_gas = gamma_gas
 

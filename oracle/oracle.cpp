@@ -43,6 +43,9 @@
 //   R13 non-periodic boundaries are transmissive: the ghost cell is the mirror
 //       image of the cell with the cell's own data, and W^ext = W^int on the
 //       boundary edge;
+//   R22 (option) the time rule of Eq. flux as two-node Gauss-Legendre, nodes
+//       dt (1/2 -+ sqrt(3)/6), weights 1/2, with the central values of Eq.
+//       timeflux from a separate Taylor evaluation at t_{n+1};
 //   R18 the scale limiter (optional, Euler): Zhang-Shu positivity scaling of
 //       the final reconstruction toward the cell average over the six edge
 //       Gauss points (density first, then pressure through the smallest
@@ -122,6 +125,7 @@ struct Params {
   double eps;       // epsilon of Eq. nonlinearweight (1e-8)
   int linear_only;  // debug: replace nonlinear weights by the linear ones
   int positivity;   // scale limiter of Zhang and Shu on the reconstruction (R18)
+  int time_rule;    // 0: Gauss-Lobatto time nodes (R2); 1: two Gauss-Legendre nodes (R22)
 };
 
 struct EdgeRec {
@@ -678,6 +682,8 @@ double spectral_radius_all(const Params& P, const double* W) {
 const double kGL = 0.28867513459481288225;  // sqrt(3)/6
 const double kTau[3] = {0.0, 0.5, 1.0};                  // R2: Lobatto nodes
 const double kWt[3] = {1.0 / 6.0, 4.0 / 6.0, 1.0 / 6.0};  // R2: Lobatto weights
+const double kTauGL[2] = {0.5 - kGL, 0.5 + kGL};          // R22: Gauss-Legendre nodes
+const double kWtGL[2] = {0.5, 0.5};                       // R22: Gauss-Legendre weights
 
 // Taylor data (W, Wt, Wtt) at the point (x, y) of a cell's own frame from the
 // cell's reconstructions rec[0..m-1] (Eq. recon, then Section 2.1).
@@ -800,9 +806,10 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
       } else {
         for (int c = 0; c < m; ++c) { We[c] = Wi[c]; Wte[c] = Wti[c]; Wtte[c] = Wtti[c]; }
       }
-      // Eqs. tay / tayext at the Lobatto nodes, LLF flux, time quadrature
-      for (int si = 0; si < 3; ++si) {
-        double tau = kTau[si] * dt;
+      // Eqs. tay / tayext at the time nodes, LLF flux, time quadrature (Eq. flux)
+      const bool gauss = pb.P.time_rule == 1;
+      for (int si = 0; si < (gauss ? 2 : 3); ++si) {
+        double tau = (gauss ? kTauGL[si] : kTau[si]) * dt;
         S a[4], b[4], Ha[4], Hb[4];
         for (int c = 0; c < m; ++c) {
           a[c] = Wi[c] + Wti[c] * S(tau) + Wtti[c] * S(0.5 * tau * tau);
@@ -812,11 +819,20 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
         flux_normal(pb.P, b, e.nx, e.ny, Hb);
         for (int c = 0; c < m; ++c) {
           S H = S(0.5) * (Hb[c] + Ha[c] - alpha * (b[c] - a[c]));
-          Fe[c] = Fe[c] + S(kWt[si] * 0.5 * e.len) * H;  // w_s * w_G * |e|
+          Fe[c] = Fe[c] + S((gauss ? kWtGL[si] : kWt[si]) * 0.5 * e.len) * H;  // w_s * w_G * |e|
         }
-        if (si == 2) {
+        if (!gauss && si == 2) {
           // Eq. timeflux: central value at t_{n+1} (Lobatto node tau = dt)
           for (int c = 0; c < m; ++c) Se[c] = Se[c] + S(0.5 * e.len) * (S(0.5) * (a[c] + b[c]));
+        }
+      }
+      if (gauss) {
+        // Eq. timeflux: the central value at t_{n+1} from its own Taylor evaluation
+        S a[4], b[4];
+        for (int c = 0; c < m; ++c) {
+          a[c] = Wi[c] + Wti[c] * S(dt) + Wtti[c] * S(0.5 * dt * dt);
+          b[c] = We[c] + Wte[c] * S(dt) + Wtte[c] * S(0.5 * dt * dt);
+          Se[c] = Se[c] + S(0.5 * e.len) * (S(0.5) * (a[c] + b[c]));
         }
       }
     }
@@ -877,7 +893,7 @@ int orc_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt, dou
   pb->P.eq = eq; pb->P.m = (eq == EQ_EULER) ? 4 : 1;
   pb->P.ax = ax; pb->P.ay = ay; pb->P.gam = gam; pb->P.cfl = cfl;
   for (int l = 0; l < 4; ++l) pb->P.glin[l] = glin ? glin[l] : (l == 0 ? 0.94 : 0.02);
-  pb->P.eps = eps; pb->P.linear_only = linear_only; pb->P.positivity = 0;
+  pb->P.eps = eps; pb->P.linear_only = linear_only; pb->P.positivity = 0; pb->P.time_rule = 0;
   for (int64_t i = 0; i < 3 * nt; ++i)
     if (tri[i] < 0 || tri[i] >= nv) { g_err = "vertex index out of range"; delete pb; return 4; }
   if (!build_connectivity(*pb, tri) || !build_geometry(*pb, xy, tri)) { delete pb; return 4; }
@@ -890,6 +906,14 @@ void orc_destroy(orc_problem* p) { delete reinterpret_cast<Problem*>(p); }
 // Switch the scale limiter (R18) on or off.
 int orc_set_positivity(orc_problem* p, int on) {
   reinterpret_cast<Problem*>(p)->P.positivity = on;
+  return 0;
+}
+
+// Time rule of the edge flux: 0 three-node Gauss-Lobatto (R2), 1 two-node
+// Gauss-Legendre (R22).
+int orc_set_time_rule(orc_problem* p, int rule) {
+  if (rule != 0 && rule != 1) { g_err = "time rule must be 0 or 1"; return 1; }
+  reinterpret_cast<Problem*>(p)->P.time_rule = rule;
   return 0;
 }
 

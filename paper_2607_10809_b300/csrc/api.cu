@@ -70,6 +70,9 @@ hw_status check_options(const hw_options* o) {
   if (o->eq == HW_EULER && !(o->gamma_gas > 1)) return fail(HW_EINVAL, "gamma_gas must exceed 1");
   if (!(o->gamma_lin[0] > 0)) return fail(HW_EINVAL, "gamma_1 must be positive");
   if (o->positivity != 0 && o->positivity != 1) return fail(HW_EINVAL, "positivity must be 0 or 1");
+  if (o->time_rule != 0 && o->time_rule != 1) return fail(HW_EINVAL, "time_rule must be 0 or 1");
+  if (o->time_rule == 1 && o->positivity)
+    return fail(HW_EINVAL, "the Gauss-Legendre time rule is not combined with the scale limiter");
   return HW_OK;
 }
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -160,6 +163,7 @@ struct hw_solver {
     a.dt_fixed = dt_fixed;
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
     a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
+    a.P.time_rule = opt.time_rule;
     for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
     eq_params_finish(a.P);
     return a;
@@ -612,6 +616,7 @@ hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* 
   if (!s || !U_n || !Ubar_next || !Ubar_n || !scratch) return fail(HW_EINVAL, "null pointer");
   if (s->eq != HW_EULER) return fail(HW_EINVAL, "the adjoint step is implemented for the Euler equations");
   if (s->opt.positivity) return fail(HW_EINVAL, "the adjoint step does not cover the scale limiter");
+  if (s->opt.time_rule != 0) return fail(HW_EINVAL, "the adjoint step follows the Gauss-Lobatto time rule only");
   if (!(dt > 0)) return fail(HW_EINVAL, "the adjoint step needs the (fixed) time step dt > 0");
   if ((reinterpret_cast<uintptr_t>(U_n) | reinterpret_cast<uintptr_t>(Pb_n) | reinterpret_cast<uintptr_t>(Ubar_next) |
        reinterpret_cast<uintptr_t>(Ubar_n)) % 16)

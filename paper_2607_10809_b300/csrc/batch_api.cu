@@ -82,6 +82,7 @@ hw_status check_batch_args(const hw_mesh* const* meshes, int32_t n, const hw_opt
   for (int k = 0; k < n; ++k)
     if (!meshes[k]) return bfail(HW_EINVAL, "null mesh in batch");
   if (opt->eq < 0 || opt->eq > 2 || !(opt->cfl > 0)) return bfail(HW_EINVAL, "bad options");
+  if (opt->time_rule != 0) return bfail(HW_EINVAL, "the batched form uses the Gauss-Lobatto time rule only");
   if (precision != HW_FP64 && precision != HW_FP32) return bfail(HW_EINVAL, "unknown precision");
   return HW_OK;
 }
@@ -131,6 +132,7 @@ struct hw_batch {
     for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
     eq_params_finish(a.P);
     a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
+    a.P.time_rule = 0;
     return a;
   }
 };

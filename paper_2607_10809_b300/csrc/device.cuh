@@ -29,6 +29,7 @@ struct EqParams {
   double ax, ay, gam, eps;
   double g[4];
   int positivity;   // scale limiter on (Euler)
+  int time_rule;    // 0: Gauss-Lobatto time nodes (0, dt/2, dt); 1: two Gauss-Legendre nodes
   // derived on the host by eq_params_finish: gamma - 1, |a|, and every
   // constant rounded once to float for the single-precision kernels (a
   // conversion or a double operation inside a kernel runs on the slow

@@ -39,7 +39,8 @@ class HwError(RuntimeError):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("eq", ctypes.c_int32), ("positivity", ctypes.c_int32), ("ax", ctypes.c_double),
+    _fields_ = [("eq", ctypes.c_int32), ("positivity", ctypes.c_int32), ("time_rule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("gamma_gas", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("gamma_lin", ctypes.c_double * 4), ("eps", ctypes.c_double)]
 
@@ -125,12 +126,16 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
+TIME_RULES = {"lobatto": 0, "gauss": 1}
+
+
 def options(eq="advection", a=(1.0, 1.0), gamma_gas=1.4, cfl=0.5, gamma_lin=(0.94, 0.02, 0.02, 0.02), eps=1e-8,
-            positivity=False):
+            positivity=False, time_rule="lobatto"):
     o = Options()
     load().hw_options_default(ctypes.byref(o))
     o.eq = EQUATIONS[eq]
     o.positivity = int(bool(positivity))
+    o.time_rule = TIME_RULES[time_rule]
     o.ax, o.ay = a
     o.gamma_gas = gamma_gas
     o.cfl = cfl

@@ -283,16 +283,18 @@ def test_lw_euler_reproduces_translating_vortex():
 
 
 # ---------------------------------------------------------------- whole step
-def test_step_exact_for_advected_quadratic_with_linear_weights():
+@pytest.mark.parametrize("time_rule", ["lobatto", "gauss"])
+def test_step_exact_for_advected_quadratic_with_linear_weights(time_rule):
     """Quadratic data + linear weights: the reconstruction is exact, the
-    second-order Taylor expansion in time is exact, the Lobatto rule is exact for
-    the quadratic time dependence and two Gauss points are exact on the edges,
-    so one step reproduces the exact cell averages of W, W_x, W_y (Eqs. flx,
-    derave2d2) away from the boundary."""
+    second-order Taylor expansion in time is exact, both time rules (three
+    Lobatto nodes, two Gauss-Legendre nodes) are exact for the quadratic time
+    dependence and two Gauss points are exact on the edges, so one step
+    reproduces the exact cell averages of W, W_x, W_y (Eqs. flx, derave2d2)
+    away from the boundary."""
     mesh = I.jittered_box(9, 1.0, seed=6)
     q = np.array([0.4, 0.9, -0.6, 1.1, 0.8, -0.7])
     a = (0.8, -0.5)
-    o = oracle.Oracle(mesh, "advection", a=a, linear_only=True)
+    o = oracle.Oracle(mesh, "advection", a=a, linear_only=True, time_rule=time_rule)
     nbr, _ = o.neighbors()
     U = I.initial_state(mesh, quad_fn(q), 1)
     dt = 0.04
@@ -304,13 +306,14 @@ def test_step_exact_for_advected_quadratic_with_linear_weights():
     np.testing.assert_allclose(Un[:, :, cells], Ue[:, :, cells], rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("time_rule", ["lobatto", "gauss"])
 @pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
-def test_conservation_on_periodic_mesh(eq):
+def test_conservation_on_periodic_mesh(eq, time_rule):
     mesh = I.jittered_periodic(8, 10.0 if eq == "euler" else 2.0, seed=12)
     m = 4 if eq == "euler" else 1
     fn = I.vortex if eq == "euler" else (I.advection_sine if eq == "advection" else I.burgers_sine)
     U = I.initial_state(mesh, fn, m)
-    o = oracle.Oracle(mesh, eq)
+    o = oracle.Oracle(mesh, eq, time_rule=time_rule)
     area = o.cell_geometry()["area"]
     s0 = (U[0] * area).sum(axis=1)
     for _ in range(4):
@@ -391,6 +394,25 @@ def test_third_order_on_smooth_advection(golden_dir):
     fine = min(min(v["order"][-2:]) for k, v in paper.items() if not k.startswith("_"))
     o = _orders(errs)
     assert o[-1] > fine - 0.1 and o[-1] < 3.3, (errs, o)
+
+
+def test_gauss_legendre_time_rule_is_third_order_and_close_to_lobatto():
+    """The two-node Gauss-Legendre time rule (with the central values of Eq.
+    timeflux from a separate Taylor evaluation at t_{n+1}) keeps third order on
+    smooth advection, and its errors stay within a factor 2 of the Lobatto
+    rule's (both integrate the quadratic Taylor polynomials exactly)."""
+    errs = {"lobatto": [], "gauss": []}
+    for n in (10, 20, 40):
+        mesh = I.config1_mesh(n)
+        U0 = I.initial_state(mesh, I.advection_sine, 1)
+        We = I.cell_averages(mesh, lambda x, y: I.advection_sine(x - 0.5, y - 0.5), 1)[0]
+        for rule in errs:
+            U, _ = oracle.Oracle(mesh, "advection", time_rule=rule).run_to(U0, 0.5)
+            errs[rule].append(I.error_norms(mesh, U[0, 0], We)[0])
+    o = _orders(errs["gauss"])
+    assert o[-1] > 2.8 and o[-1] < 3.3, (errs, o)
+    ratio = np.array(errs["gauss"]) / np.array(errs["lobatto"])
+    assert np.all(ratio > 0.5) and np.all(ratio < 2.0), ratio
 
 
 def test_burgers_and_vortex_converge():
