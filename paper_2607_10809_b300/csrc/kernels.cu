@@ -405,10 +405,14 @@ template <typename R, int EQ> constexpr size_t edge_smem_bytes() {
          sizeof(R) * EqTraits<EQ>::m * kCells + 2 * sizeof(uint64_t) + 128;
 }
 
-// Flux at the Gauss-Lobatto time nodes, cell-average and Green-Gauss update,
-// CFL candidates over the context's tiles.  Returns false if a bounded wait
-// gave up.
-template <typename R, int EQ, typename Ctx>
+// Flux at the time nodes, cell-average and Green-Gauss update, CFL candidates
+// over the context's tiles.  GL = false: the three Gauss-Lobatto nodes, the
+// last of which (t_{n+1}) also gives the central values of Eq. timeflux; GL =
+// true: two Gauss-Legendre nodes and a separate Taylor evaluation at t_{n+1}.
+// Returns false if a bounded wait gave up.
+constexpr double kGaussNode = 0.28867513459481288225;   // sqrt(3) / 6
+
+template <typename R, int EQ, bool GL, typename Ctx>
 __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap* mIdx, const EqParams& P,
                            const R* __restrict__ Pb, unsigned char* base, uint64_t* bar, unsigned* ph) {
   constexpr int m = EqTraits<EQ>::m;
@@ -491,13 +495,20 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
           b1[c] = left ? theirs[m + c] : mine[m + c];
           b2[c] = left ? theirs[2 * m + c] : mine[2 * m + c];
         }
-        const R tau[3] = {R(0), R(0.5) * dtr, dtr};
-        const R wts[3] = {R(1.0 / 6.0), R(4.0 / 6.0), R(1.0 / 6.0)};
+        constexpr int ns = GL ? 2 : 3;   // time nodes
+        R tau[3], wts[3];
+        if constexpr (GL) {
+          tau[0] = dtr * R(0.5 - kGaussNode); tau[1] = dtr * R(0.5 + kGaussNode);
+          wts[0] = R(0.5); wts[1] = R(0.5);
+        } else {
+          tau[0] = R(0); tau[1] = R(0.5) * dtr; tau[2] = dtr;
+          wts[0] = R(1.0 / 6.0); wts[1] = R(4.0 / 6.0); wts[2] = R(1.0 / 6.0);
+        }
         R Fe[m], Sh[m];
 #pragma unroll
         for (int c = 0; c < m; ++c) Fe[c] = R(0);
 #pragma unroll
-        for (int si = 0; si < 3; ++si) {
+        for (int si = 0; si < ns; ++si) {
           R WL[m], WR[m], HL[m], HR[m];
           const R hs = R(0.5) * tau[si] * tau[si];
 #pragma unroll
@@ -509,10 +520,16 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
           flux_n<R, EQ>(WR, nx, ny, P, HR);
 #pragma unroll
           for (int c = 0; c < m; ++c) Fe[c] += wts[si] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
-          if (si == 2) {
+          if (!GL && si == 2) {
 #pragma unroll
             for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
           }
+        }
+        if constexpr (GL) {   // Eq. timeflux from its own Taylor evaluation at t_{n+1}
+          const R hs = R(0.5) * dtr * dtr;
+#pragma unroll
+          for (int c = 0; c < m; ++c)
+            Sh[c] = R(0.5) * ((a0[c] + dtr * a1[c] + hs * a2[c]) + (b0[c] + dtr * b1[c] + hs * b2[c]));
         }
         // Gauss weight 1/2 and the cell's outward normal (+-n).  In FP32 the
         // Green-Gauss terms are taken relative to the cell's own average: the
@@ -601,7 +618,7 @@ __global__ void __launch_bounds__(LIM ? kThreads : kLeanThreads) k_recon(const _
   recon_phase<R, EQ, LIM, LIM ? kThreads : kLeanThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
 }
 
-template <typename R, int EQ>
+template <typename R, int EQ, bool GL>
 __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUtensorMap mEgeo,
                                                     const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
                                                     const R* __restrict__ U, R* __restrict__ Un,
@@ -632,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUten
   }
   __syncthreads();
   unsigned ph[2] = {0u, 0u};
-  if (!edge_phase<R, EQ>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph)) ctx.local_min = dinf();
+  if (!edge_phase<R, EQ, GL>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph)) ctx.local_min = dinf();
   finish_step(sc, ctx.local_min, dt, true);
 }
 
@@ -708,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUte
     ok = recon_phase<R, EQ, LIM, kThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
     if (!grid_barrier(ctl, spin_limit, skip || !ok)) ok = false;
     if (!ok) break;
-    ok = edge_phase<R, EQ>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph);
+    ok = edge_phase<R, EQ, false>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph);
     if (!grid_barrier(ctl, spin_limit, !ok)) ok = false;
     if (!ok) break;
     // per-solve step, status and next time step (one thread per solve)
@@ -906,14 +923,15 @@ template <typename R, int EQ, bool LIM> int recon_cap() {
   static const int cap = resident_blocks(k_recon<R, EQ, LIM>, LIM ? kThreads : kLeanThreads, recon_smem_bytes<R, EQ>());
   return cap;
 }
-template <typename R, int EQ> int edge_cap() {
-  static const int cap = resident_blocks(k_edge<R, EQ>, kThreads, edge_smem_bytes<R, EQ>());
+template <typename R, int EQ, bool GL> int edge_cap() {
+  static const int cap = resident_blocks(k_edge<R, EQ, GL>, kThreads, edge_smem_bytes<R, EQ>());
   return cap;
 }
 template <typename R, int EQ> void prepare_t() {
   (void)recon_cap<R, EQ, false>();
   if constexpr (EQ == kEqEuler) (void)recon_cap<R, EQ, true>();
-  (void)edge_cap<R, EQ>();
+  (void)edge_cap<R, EQ, false>();
+  (void)edge_cap<R, EQ, true>();
 }
 
 template <typename R, int EQ, bool LIM> void launch_recon_lim(const StepArgs& a, cudaStream_t st) {
@@ -934,14 +952,18 @@ template <typename R, int EQ> void launch_recon_t(const StepArgs& a, cudaStream_
   }
   launch_recon_lim<R, EQ, false>(a, st);
 }
-template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
+template <typename R, int EQ, bool GL> void launch_edge_rule(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
   constexpr size_t smem = edge_smem_bytes<R, EQ>();
-  const int cap = edge_cap<R, EQ>();
+  const int cap = edge_cap<R, EQ, GL>();
   const int nt = a.tiles.ntiles;
-  k_edge<R, EQ><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
+  k_edge<R, EQ, GL><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
       a.maps->egeo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
       reinterpret_cast<const R*>(a.Pb), reinterpret_cast<R*>(a.C), a.P, a.sc, a.dt_fixed, a.tiles);
+}
+template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
+  if (a.P.time_rule == 1) launch_edge_rule<R, EQ, true>(a, st);
+  else launch_edge_rule<R, EQ, false>(a, st);
 }
 template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};

@@ -87,3 +87,30 @@ def test_coarsest_mesh_of_the_table_matches_the_oracle(case):
     err = (np.abs(Ug - Uo).max(axis=-1) / np.maximum(np.abs(Uo).max(axis=-1), 1e-300)).max()
     print(f"{case}, {mesh.nt} triangles, {n} steps: relative Linf {err:.2e}")
     assert err < 1e-12
+
+
+def test_density_wave_with_the_gauss_legendre_time_rule():
+    """Ablation of the time rule on the density wave (Table ex4.12d sizes):
+    the two-node Gauss-Legendre rule with a separate t_{n+1} evaluation keeps
+    third order and errors close to the default Lobatto rule's."""
+    key, eq, m, L, ns, fn, exact, T = CASES["density_wave"]
+    rows = []
+    for n in ns[:4]:
+        mesh = I.jittered_periodic(n, L, 0.15, seed=100 + n)
+        U0 = I.initial_state(mesh, fn, m)
+        We = I.cell_averages(mesh, exact(T), m)[0]
+        e = {}
+        for rule in ("lobatto", "gauss"):
+            s = hweno.Solver(mesh, U0, eq=eq, precision="fp64", time_rule=rule)
+            s.run_to(T)
+            e[rule] = I.error_norms(mesh, s.get_state()[0][0][0], We)[0]
+            s.close()
+        rows.append((mesh.nt, e["lobatto"], e["gauss"]))
+    print("\ndensity wave, L1 of the density: N, Lobatto, Gauss-Legendre")
+    for r in rows:
+        print(f"{r[0]:8d}  {r[1]:.3e}  {r[2]:.3e}")
+    g = np.array([r[2] for r in rows]); N = np.array([r[0] for r in rows], float)
+    o = np.log(g[:-1] / g[1:]) / (0.5 * np.log(N[1:] / N[:-1]))
+    assert o[-1] > 2.6, o
+    ratio = g / np.array([r[1] for r in rows])
+    assert np.all(ratio > 0.5) and np.all(ratio < 2.0), ratio

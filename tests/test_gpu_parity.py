@@ -182,3 +182,44 @@ def test_euler_riemann_with_scale_limiter(precision):
         err = np.abs(Ug[0] - Uo[0]).max(axis=1) / np.abs(Uo[0]).max(axis=1)
         print("FP32 limited Riemann rel Linf per component", err)
         assert np.all(err < 1e-3)
+
+
+@pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
+def test_gauss_legendre_time_rule_matches_oracle(eq):
+    """The two-node Gauss-Legendre time rule (a template variant of the edge
+    kernel) against the oracle with the same rule: FP64 after the full run at
+    1e-12, FP32 within the FP32 bounds of the default rule."""
+    L = 10.0 if eq == "euler" else 2.0
+    mesh = I.jittered_periodic(13, L, 0.15, seed=81)   # 338 cells: several tiles and a ragged tail
+    m = 4 if eq == "euler" else 1
+    fn = I.vortex if eq == "euler" else (I.advection_sine if eq == "advection" else I.burgers_sine)
+    T = 0.4 if eq == "euler" else 0.1
+    U0 = I.initial_state(mesh, fn, m)
+    Uo, dts = oracle.Oracle(mesh, eq, time_rule="gauss").run_to(U0, T)
+    Ul, _ = oracle.Oracle(mesh, eq).run_to(U0, T)
+    if eq == "advection":
+        # linear flux of quadratic Taylor data: both rules integrate it exactly
+        assert rel_linf(Uo, Ul) < 1e-12
+    else:
+        # the rules differ (higher-degree integrands): the comparison below is not vacuous
+        assert rel_linf(Uo, Ul) > 1e-13
+    s = hweno.Solver(mesh, U0, eq=eq, precision="fp64", time_rule="gauss")
+    assert s.run_to(T) == len(dts)
+    Ug, t = s.get_state()
+    assert rel_linf(Ug, Uo) < FP64_TOL
+    s32 = hweno.Solver(mesh, U0, eq=eq, precision="fp32", time_rule="gauss")
+    s32.run_to(T)
+    U32, _ = s32.get_state()
+    err = np.abs(U32[0] - Uo[0]).max(axis=1) / np.abs(Uo[0]).max(axis=1)
+    print(f"Gauss-Legendre time rule, {eq}: FP64 {rel_linf(Ug, Uo):.2e}, FP32 W {err.max():.2e}")
+    assert err.max() < 1e-5
+
+
+def test_gauss_legendre_time_rule_refused_by_the_adjoint():
+    mesh = I.jittered_periodic(5, 10.0, seed=1)
+    U0 = I.initial_state(mesh, I.vortex, 4)
+    s = hweno.Solver(mesh, U0, eq="euler", precision="fp64", time_rule="gauss")
+    a, b = s.state_buffer(), s.state_buffer()
+    with pytest.raises(hweno.HwError) as e:
+        s.step_adjoint(0.01, a, b, a, s.adjoint_scratch())
+    assert e.value.status == hweno.HW_EINVAL

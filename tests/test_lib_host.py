@@ -125,3 +125,24 @@ def test_empty_and_degenerate_inputs_are_rejected(lib):
     b = ctypes.c_void_p()
     rc = L.hw_batch_create(None, 0, ctypes.byref(o), 1, None, None, None, None, 0, None, ctypes.byref(b))
     assert rc == hweno.HW_EINVAL and b"empty" in L.hw_last_error()
+
+
+def test_time_rule_option_is_checked(lib):
+    """The Gauss-Legendre time rule is accepted by the single-solve path, and
+    refused with the scale limiter, by the batched form, and as an unknown
+    value."""
+    mesh = hweno.Mesh(I.jittered_periodic(6, 10.0, seed=2))
+    assert hweno.hw_workspace_bytes(mesh.h, hweno.options("euler", time_rule="gauss"), "fp32") > 0
+    for bad in (hweno.options("euler", time_rule="gauss", positivity=True),):
+        with pytest.raises(hweno.HwError) as e:
+            hweno.hw_workspace_bytes(mesh.h, bad, "fp32")
+        assert e.value.status == hweno.HW_EINVAL
+    o = hweno.options("euler"); o.time_rule = 2
+    with pytest.raises(hweno.HwError):
+        hweno.hw_workspace_bytes(mesh.h, o, "fp32")
+    L = hweno.load()
+    arr = (ctypes.c_void_p * 1)(mesh.h)
+    n = ctypes.c_size_t()
+    og = hweno.options("euler", time_rule="gauss")
+    assert L.hw_batch_workspace_bytes(arr, 1, ctypes.byref(og), 1, ctypes.byref(n)) == hweno.HW_EINVAL
+    assert b"Gauss-Lobatto" in L.hw_last_error()
