@@ -5,8 +5,9 @@
 //             Lax-Wendroff procedure of Section 2.1; writes the Taylor data
 //             (W, W_t, W_tt) of Eqs. tay / tayext to the edge-point buffer.
 //   k_edge  : per cell (owner computes, no atomics), at the six Gauss points
-//             of its edges the local Lax-Friedrichs flux at the Gauss-Lobatto
-//             time nodes (Eqs. fx, flux) in a canonical orientation, so both
+//             of its edges the local Lax-Friedrichs flux at the time nodes
+//             (Eqs. fx, flux; Gauss-Lobatto, or as an option two Gauss-Legendre
+//             nodes) in a canonical orientation, so both
 //             cells of an edge obtain bitwise-identical values; the update of
 //             the cell average (Eq. flx) and of the derivative averages by
 //             Green-Gauss from the central values at t_{n+1} (Eqs. derave2d2,

@@ -12,7 +12,7 @@ namespace hw {
 
 constexpr int kConsvBlocks = 296;                  // 2 x 148 SMs, fixed so the summation order is fixed
 constexpr int kCells = 32;                         // cells per tile; plane strides are multiples of it
-constexpr int kThreads = 6 * kCells;               // 6 threads per cell (batched kernel, scale limiter)
+constexpr int kThreads = 6 * kCells;               // 6 threads per cell (k_edge, batched kernel, scale limiter)
 constexpr int kLeanThreads = 2 * kCells;           // single-solve reconstruction: 2 threads per cell, so
                                                    // that the (cell, component) and (cell, point) task sets
                                                    // of a tile fill whole passes (2 and 3 for the Euler system)
