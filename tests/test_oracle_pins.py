@@ -325,9 +325,10 @@ def test_conservation_on_periodic_mesh(eq, time_rule):
     assert np.all(np.abs((U[2] * area).sum(axis=1)) < 1e-13 * scale)
 
 
+@pytest.mark.parametrize("time_rule", ["lobatto", "gauss"])
 @pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
 @pytest.mark.parametrize("kind", ["jittered", "poisson", "box"])
-def test_free_stream_preserved(eq, kind):
+def test_free_stream_preserved(eq, kind, time_rule):
     if kind == "jittered":
         mesh = I.jittered_periodic(7, 1.0, seed=21)
     elif kind == "poisson":
@@ -337,7 +338,7 @@ def test_free_stream_preserved(eq, kind):
     m = 4 if eq == "euler" else 1
     const = {"advection": [2.5], "burgers": [0.7], "euler": list(I.euler_from_primitive(1.3, 0.4, -0.7, 0.9))}[eq]
     U = np.zeros((3, m, mesh.nt)); U[0] = np.array(const)[:, None]
-    o = oracle.Oracle(mesh, eq)
+    o = oracle.Oracle(mesh, eq, time_rule=time_rule)
     U1 = U
     for _ in range(3):
         U1 = o.step(U1, o.cfl_dt(U1))
