@@ -80,8 +80,9 @@ typedef struct {
   double ax, ay;        /* advection velocity (HW_ADVECTION) */
   double gamma_gas;     /* ratio of specific heats (HW_EULER) */
   double cfl;           /* dt = cfl * min_K inradius_K / lambda_K */
-  double gamma_lin[4];  /* linear weights gamma_1..gamma_4, sum 1 */
-  double eps;           /* epsilon in the nonlinear weights */
+  double gamma_lin[4];  /* linear weights gamma_1..gamma_4: each > 0 and sum 1 within
+                           1e-12 (Section 2.2, Step 3); HW_EINVAL otherwise */
+  double eps;           /* epsilon in the nonlinear weights, > 0 */
 } hw_options;
 
 typedef struct hw_mesh hw_mesh;
@@ -127,7 +128,9 @@ hw_status hw_workspace_bytes(const hw_mesh* mesh, const hw_options* opt, int32_t
 /* Upload geometry and the initial state (host arrays as described above) into
  * the caller's workspace and compute the first CFL time step.  The workspace
  * must stay valid until hw_solver_destroy.  cuda_stream: cudaStream_t (NULL =
- * legacy default stream).  Synchronises the stream before returning. */
+ * legacy default stream).  Synchronises the stream before returning.  The
+ * first call on a device also commits the library's static scratch array of
+ * hw_step_static_scratch there (64 MiB, held until the process exits). */
 hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t precision, const double* Wbar,
                         const double* Vbar, const double* Ybar, void* workspace, size_t workspace_bytes,
                         void* cuda_stream, hw_solver** out);
@@ -173,12 +176,14 @@ hw_status hw_solver_destroy(hw_solver* s);
  * pool, plug-ins handed fixed buffers, runtimes that must not allocate while
  * running); they still pass the state and geometry through the solver's
  * workspace, but need no memory for temporaries.
- *   - Limit: 18 * m * ntri * (8 for FP64, 4 for FP32) bytes must fit in the
- *     64 MiB array (FP32 Euler: 233,016 triangles; FP64 Euler: 116,508);
- *     larger meshes get HW_EINVAL with a message naming both sizes.
- *   - The array is reserved on every GPU that loads the library, until exit.
- *   - The first call on a device looks up the array's device address with that
- *     device current; make that first call before any stream capture.
+ *   - Limit: 18 * m * ld * (8 for FP64, 4 for FP32) bytes must fit in the
+ *     64 MiB array, where ld is ntri rounded up to a multiple of 32 (FP32
+ *     Euler: at most 232,992 triangles; FP64 Euler: at most 116,480); larger
+ *     meshes get HW_EINVAL with a message naming both sizes.
+ *   - The array's 64 MiB are committed on a device by the first hw_state_init
+ *     on that device (which also looks up the array's device address there)
+ *     and stay reserved until the process exits; hw_step_static_scratch itself
+ *     makes no allocation of any kind.
  *   - All calls share the one array and it keeps the last call's contents
  *     (every slot a step reads is written earlier in the same step, so nothing
  *     needs clearing); calls whose work overlaps on the GPU (other streams,

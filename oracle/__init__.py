@@ -57,6 +57,9 @@ def lib():
         _lib.orc_lax_wendroff.argtypes = [ctypes.c_int, d, d, d, vp, vp]
         _lib.orc_cell_taylor.argtypes = [vp, vp, d, i64, vp]
         _lib.orc_flux_derivs.argtypes = [ctypes.c_int, d, d, d, vp, vp, vp, vp]
+        _lib.orc_spectral_radius.argtypes = [ctypes.c_int, d, d, d, vp, d, d, vp]
+        _lib.orc_admissible_fraction.argtypes = [d, vp, vp, d]
+        _lib.orc_admissible_fraction.restype = d
         _lib.orc_last_error.restype = ctypes.c_char_p
     return _lib
 
@@ -182,3 +185,17 @@ def flux_derivs(eq: str, W, da, db, a=(1.0, 1.0), gamma_gas: float = 1.4):
     out = np.empty((6, W.shape[0]))
     _check(lib().orc_flux_derivs(EQ[eq], a[0], a[1], gamma_gas, _ptr(W), _ptr(da), _ptr(db), _ptr(out)))
     return out
+
+
+def spectral_radius(eq: str, W, n, a=(1.0, 1.0), gamma_gas: float = 1.4):
+    """(largest |eigenvalue| of d(F.n)/dW for the unit normal n, largest over all directions)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.empty(2)
+    _check(lib().orc_spectral_radius(EQ[eq], a[0], a[1], gamma_gas, _ptr(W), float(n[0]), float(n[1]), _ptr(out)))
+    return float(out[0]), float(out[1])
+
+
+def admissible_fraction(Wb, w, eps, gamma_gas: float = 1.4):
+    """Largest f in [0, 1] with density and pressure >= eps on Wb + f (w - Wb)."""
+    Wb = np.ascontiguousarray(Wb, dtype=np.float64); w = np.ascontiguousarray(w, dtype=np.float64)
+    return float(lib().orc_admissible_fraction(gamma_gas, _ptr(Wb), _ptr(w), float(eps)))

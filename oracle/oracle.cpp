@@ -523,29 +523,26 @@ template <class S> S pressure(double gam, const S* W) {
   return S(gam - 1.0) * (W[3] - S(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
 }
 
-// Smallest non-negative root, clamped to 1, of the pressure condition along
-// the segment Wb + f d: (gam-1) [(E0 + f dE)(r0 + f dr) - |m0 + f dm|^2 / 2]
-// - eps (r0 + f dr) = a f^2 + b f + c0 = 0 (R18).  Clamping makes the factor
-// tend to 1 as the point value approaches the admissible boundary.
+// Largest f in [0, 1] with p(Wb + f d) >= eps along the segment from the cell
+// average Wb (R18), by bisection on the pressure itself.  Where the density is
+// positive the pressure is a concave function of the conservative variables,
+// so the admissible part of the segment is an interval [0, f*] (p(Wb) > eps
+// at its start); f* is where p first falls to eps.  The limiter is not
+// differentiated (the adjoint excludes it), so the search runs on the values.
 template <class S> S pressure_root(double gam, const S Wb[4], const S d[4], double eps) {
-  const S g1 = S(gam - 1.0);
-  const S a = g1 * (d[3] * d[0] - S(0.5) * (d[1] * d[1] + d[2] * d[2]));
-  const S b = g1 * (Wb[3] * d[0] + Wb[0] * d[3] - (Wb[1] * d[1] + Wb[2] * d[2])) - S(eps) * d[0];
-  const S c0 = g1 * (Wb[3] * Wb[0] - S(0.5) * (Wb[1] * Wb[1] + Wb[2] * Wb[2])) - S(eps) * Wb[0];
-  S tk = S(0.0);
-  if (std::fabs(val(a)) < 1e-300) {
-    if (val(b) < 0) tk = S(0.0) - c0 / b;
-    if (val(tk) > 1) tk = S(1.0);
-  } else {
-    const S disc = b * b - S(4.0) * a * c0;
-    const S sq = val(disc) > 0 ? sqrt(disc) : S(0.0);
-    const S r1 = (S(0.0) - b - sq) / (S(2.0) * a), r2 = (S(0.0) - b + sq) / (S(2.0) * a);
-    S best = S(-1.0);
-    if (val(r1) >= 0) best = r1;
-    if (val(r2) >= 0 && (val(best) < 0 || val(r2) < val(best))) best = r2;
-    tk = val(best) < 0 ? S(0.0) : (val(best) > 1 ? S(1.0) : best);
+  auto p_at = [&](double f) {
+    double w[4];
+    for (int c = 0; c < 4; ++c) w[c] = val(Wb[c]) + f * val(d[c]);
+    return (gam - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+  };
+  if (p_at(1.0) >= eps) return S(1.0);
+  double lo = 0.0, hi = 1.0;   // p_at(lo) >= eps > p_at(hi)
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;   // lo and hi are adjacent doubles
+    if (p_at(mid) >= eps) lo = mid; else hi = mid;
   }
-  return tk;
+  return S(lo);
 }
 
 // Positivity-preserving scaling of Zhang and Shu (the "scale limiter" of
@@ -1055,6 +1052,23 @@ int orc_lax_wendroff(int eq, double ax, double ay, double gam, const double* jet
     out[c] = Wt[c]; out[P.m + c] = Wtx[c]; out[2 * P.m + c] = Wty[c]; out[3 * P.m + c] = Wtt[c];
   }
   return 0;
+}
+
+// Spectral radii at W (R10, R12): out[0] = largest |eigenvalue| of
+// d(F.n)/dW for the unit normal (nx, ny), out[1] = the largest over all
+// directions.
+int orc_spectral_radius(int eq, double ax, double ay, double gam, const double* W, double nx, double ny, double* out) {
+  Params P{};
+  P.eq = eq; P.m = (eq == EQ_EULER) ? 4 : 1; P.ax = ax; P.ay = ay; P.gam = gam;
+  out[0] = spectral_radius_n<double>(P, W, nx, ny);
+  out[1] = spectral_radius_all(P, W);
+  return 0;
+}
+
+// Scale-limiter fraction (R18): the largest f in [0, 1] such that
+// Wb + f (w - Wb) has density and pressure >= eps (Euler, gamma gam).
+double orc_admissible_fraction(double gam, const double* Wb, const double* w, double eps) {
+  return admissible_fraction<double>(gam, Wb, w, eps);
 }
 
 // Flux directional derivatives at W: out[6][m] = f'a, f'b, f''[a]b, g'a, g'b, g''[a]b

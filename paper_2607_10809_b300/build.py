@@ -51,10 +51,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.check_call([NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                                "-Xlinker", "-rpath=/usr/local/cuda/lib64"])
         os.replace(tmp, LIB)
-    probe_src = os.path.join(HERE, "probes", "alu_peaks.cu")
-    probe = os.path.join(OUT_DIR, "alu_peaks")
-    if force or _stale(probe, [probe_src]):
-        subprocess.check_call([NVCC, *ARCH, "-O3", "-o", probe, probe_src])
     return LIB
 
 

@@ -3,6 +3,7 @@
 // steps, and run_to through a captured CUDA graph of several steps.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -68,7 +69,14 @@ hw_status check_options(const hw_options* o) {
   if (o->eq < 0 || o->eq > 2) return fail(HW_EINVAL, "unknown equation");
   if (!(o->cfl > 0)) return fail(HW_EINVAL, "cfl must be positive");
   if (o->eq == HW_EULER && !(o->gamma_gas > 1)) return fail(HW_EINVAL, "gamma_gas must exceed 1");
-  if (!(o->gamma_lin[0] > 0)) return fail(HW_EINVAL, "gamma_1 must be positive");
+  // Section 2.2, Step 3: the linear weights are positive and sum to one
+  double gsum = 0.0;
+  for (int l = 0; l < 4; ++l) {
+    if (!(o->gamma_lin[l] > 0)) return fail(HW_EINVAL, "every linear weight gamma_l must be positive");
+    gsum += o->gamma_lin[l];
+  }
+  if (!(std::fabs(gsum - 1.0) <= 1e-12)) return fail(HW_EINVAL, "the linear weights must sum to 1");
+  if (!(o->eps > 0)) return fail(HW_EINVAL, "eps must be positive");
   if (o->positivity != 0 && o->positivity != 1) return fail(HW_EINVAL, "positivity must be 0 or 1");
   if (o->time_rule != 0 && o->time_rule != 1) return fail(HW_EINVAL, "time_rule must be 0 or 1");
   if (o->time_rule == 1 && o->positivity)
@@ -106,6 +114,12 @@ hw_status encode_planes(CUtensorMap* map, CUtensorMapDataType dt, size_t esize, 
   if (r != CUDA_SUCCESS) return fail(HW_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
   return HW_OK;
 }
+}  // namespace
+
+namespace {
+// Device address of the static scratch array of hw_step_static_scratch on the
+// current device (defined with the array below).
+hw_status static_scratch_address(void** out);
 }  // namespace
 
 void hw_set_last_error_internal(const char* msg) { g_last_error = msg ? msg : ""; }
@@ -294,6 +308,11 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
   if (hw_status st = hw_encode_plane_maps(&s->maps, precision, s->ws + s->L.rgeo, s->ws + s->L.igeo, M.nt, s->ld))
     return bail(st);
   prepare_step_kernels(precision, s->eq);
+  // Look up the static scratch array of hw_step_static_scratch on this device
+  // now: the lookup loads the module that holds the array, which commits its
+  // memory, so that a later step without caller scratch allocates nothing.
+  void* scratch = nullptr;
+  if (hw_status st = static_scratch_address(&scratch)) return bail(st);
   s->cur = 0;
   if (hw_status st = upload_state(s, Wbar, Vbar, Ybar, 0.0)) return bail(st);
   if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
@@ -500,6 +519,7 @@ hw_status static_scratch_address(void** out) {
 
 extern "C" hw_status hw_step_static_scratch(hw_solver* s, double dt) {
   if (!s) return fail(HW_EINVAL, "null solver");
+  // the edge-point buffer spans the padded plane stride ld (ntri rounded up to a multiple of 32)
   const size_t need = (size_t)18 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4);
   if (need > kStaticScratchBytes)
     return fail(HW_EINVAL, "hw_step_static_scratch: the mesh needs " + std::to_string(need) +

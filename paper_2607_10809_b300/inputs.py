@@ -80,6 +80,20 @@ def jittered_periodic(n: int, L: float, jitter: float = 0.15, seed: int = 0) -> 
     return Mesh(xy=xy, tri=tri, Lx=L, Ly=L, bc=0)
 
 
+def jittered_periodic_rect(nx: int, ny: int, h: float, jitter: float = 0.15, seed: int = 0) -> Mesh:
+    """Periodic [0, nx h) x [0, ny h) grid of nx x ny squares (2 nx ny
+    triangles) whose vertices move by U(-jitter*h, +jitter*h) per coordinate."""
+    if nx < 3 or ny < 3:
+        raise ValueError("need at least 3 squares per direction on a torus")
+    rng = np.random.default_rng(seed)
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    xy = np.stack([I.ravel() * h, J.ravel() * h], axis=1).astype(np.float64)
+    if jitter > 0:
+        xy += rng.uniform(-jitter * h, jitter * h, size=xy.shape)
+    tri = _grid_triangles(nx, ny, lambda i, j: (i % nx) * ny + (j % ny))
+    return Mesh(xy=xy, tri=tri, Lx=nx * h, Ly=ny * h, bc=0)
+
+
 def jittered_box(n: int, L: float = 1.0, jitter: float = 0.15, seed: int = 0) -> Mesh:
     """Non-periodic [0, L]^2 grid (transmissive boundaries).  Interior vertices
     move by U(+-jitter*h) per coordinate, boundary vertices only along the

@@ -146,3 +146,19 @@ def test_time_rule_option_is_checked(lib):
     og = hweno.options("euler", time_rule="gauss")
     assert L.hw_batch_workspace_bytes(arr, 1, ctypes.byref(og), 1, ctypes.byref(n)) == hweno.HW_EINVAL
     assert b"Gauss-Lobatto" in L.hw_last_error()
+
+
+@pytest.mark.parametrize("weights,why", [
+    ((0.94, 0.02, 0.02, 0.0), "a zero linear weight"),
+    ((0.98, 0.03, 0.02, -0.03), "a negative linear weight"),
+    ((0.94, 0.02, 0.02, 0.03), "weights summing to 1.01"),
+    ((0.5, 0.2, 0.2, 0.09), "weights summing to 0.99"),
+])
+def test_linear_weights_must_be_positive_and_sum_to_one(lib, weights, why):
+    # Section 2.2, Step 3: any positive linear weights summing to one
+    m = hweno.Mesh(I.config1_mesh(4))
+    with pytest.raises(hweno.HwError) as e:
+        hweno.hw_workspace_bytes(m.h, hweno.options("advection", gamma_lin=weights), "fp64")
+    assert e.value.status == hweno.HW_EINVAL, why
+    assert "linear weight" in str(e.value)
+    hweno.hw_workspace_bytes(m.h, hweno.options("advection", gamma_lin=(0.7, 0.1, 0.1, 0.1)), "fp64")

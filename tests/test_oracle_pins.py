@@ -527,3 +527,126 @@ def test_scale_limiter_keeps_a_riemann_problem_positive_and_conservative():
     for _ in range(5):
         Up = limp.step(Up, limp.cfl_dt(Up))
     np.testing.assert_allclose((Up[0] * ap).sum(axis=1), s0, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- LLF viscosity and CFL speed
+def _random_euler_states(rng, n):
+    rho = rng.uniform(0.05, 3.0, n); u = rng.uniform(-3, 3, n); v = rng.uniform(-3, 3, n)
+    p = rng.uniform(0.01, 4.0, n)
+    return I.euler_from_primitive(rho, u, v, p).T
+
+
+def test_llf_viscosity_is_the_spectral_radius_of_the_normal_jacobian():
+    """R10: alpha is the largest |eigenvalue| of d(F.n)/dW = A nx + B ny (the
+    LLF flux of Section 2.1), checked against the eigenvalues of the textbook
+    Euler Jacobians; R12: the CFL speed is its maximum over all directions."""
+    rng = np.random.default_rng(17)
+    for W in _random_euler_states(rng, 25):
+        A, B = euler_jacobians(W)
+        th = rng.uniform(0, 2 * np.pi)
+        n = (np.cos(th), np.sin(th))
+        lam_n, lam_all = oracle.spectral_radius("euler", W, n)
+        ref = np.abs(np.linalg.eigvals(A * n[0] + B * n[1])).max()
+        assert abs(lam_n - ref) <= 1e-12 * ref, (lam_n, ref)
+        thetas = np.linspace(0, 2 * np.pi, 3601)
+        over = max(np.abs(np.linalg.eigvals(A * np.cos(t) + B * np.sin(t))).max() for t in thetas[::40])
+        dense = max(oracle.spectral_radius("euler", W, (np.cos(t), np.sin(t)))[0] for t in thetas)
+        assert over <= lam_all * (1 + 1e-12)
+        assert lam_all <= dense * (1 + 1e-5)
+    # scalar equations: |f'(u) nx + g'(u) ny|
+    for u in rng.uniform(-2, 2, 6):
+        th = rng.uniform(0, 2 * np.pi); n = (np.cos(th), np.sin(th))
+        lam_n, lam_all = oracle.spectral_radius("burgers", np.array([u]), n)
+        assert abs(lam_n - abs(u * (n[0] + n[1]))) <= 1e-15
+        assert abs(lam_all - np.sqrt(2) * abs(u)) <= 1e-15
+        lam_n, lam_all = oracle.spectral_radius("advection", np.array([u]), n, a=(0.7, -1.3))
+        assert abs(lam_n - abs(0.7 * n[0] - 1.3 * n[1])) <= 1e-15
+        assert abs(lam_all - np.hypot(0.7, 1.3)) <= 1e-15
+
+
+# ---------------------------------------------------------------- Eq. nonlinearweight
+def _jump_with_flat_side():
+    """Data with a jump through the stencil of some cells while one side of it
+    is flat: several smoothness indicators vanish there, so the epsilon term
+    of Eq. nonlinearweight decides those weights."""
+    mesh = I.jittered_box(12, 1.0, seed=8)
+    fn = lambda x, y: (1.5 + 0.8 * (x + 0.3 * y > 0.55))[None] * 1.0
+    return mesh, I.initial_state(mesh, fn, 1)
+
+
+def test_nonlinear_weights_invariant_under_scaling_of_the_data():
+    """Eq. nonlinearweight is homogeneous: under W -> s W the indicators scale
+    by s^2, kappa and both terms of the denominator by s^4 (W_ave is the mean
+    of the stencil averages), so the weights do not change (the 1e-30 of
+    W_ave is negligible here).  A wrong power of W_ave in either term, or of
+    the sum in kappa, breaks the invariance."""
+    mesh, U = _jump_with_flat_side()
+    o = oracle.Oracle(mesh)
+    geo = o.cell_geometry()
+    near = np.nonzero(np.abs(geo["cx"] + 0.3 * geo["cy"] - 0.55) < 0.08)[0]
+    moved = 0
+    for cell in near:
+        r1 = o.reconstruct_cell(U, int(cell))
+        if np.abs(r1["omega"] - np.array([0.94, 0.02, 0.02, 0.02])).max() > 1e-3:
+            moved += 1
+        for s in (1e-3, 7.0, 1e3):
+            rs = o.reconstruct_cell(s * U, int(cell))
+            np.testing.assert_allclose(rs["beta"], s * s * r1["beta"], rtol=1e-12, atol=1e-300)
+            np.testing.assert_allclose(rs["omega"], r1["omega"], rtol=1e-13, atol=1e-15)
+    assert moved >= 5
+
+
+def test_nonlinear_weights_hand_case():
+    """Eq. nonlinearweight on the oracle's own indicators of one cell, with the
+    stencil mean taken from the cell averages: omega_l proportional to
+    gamma_l (1 + kappa / (eps W_ave^4 + W_ave^2 beta_l))."""
+    mesh, U = _jump_with_flat_side()
+    o = oracle.Oracle(mesh)
+    nbr, _ = o.neighbors()
+    geo = o.cell_geometry()
+    near = np.nonzero(np.abs(geo["cx"] + 0.3 * geo["cy"] - 0.55) < 0.08)[0]
+    cell = int(min(near, key=lambda k: o.reconstruct_cell(U, int(k))["omega"][0]))
+    r = o.reconstruct_cell(U, cell)
+    b = r["beta"]
+    st = [cell] + [int(k) if k >= 0 else cell for k in nbr[cell]]
+    Wave = U[0, 0, st].mean() + 1e-30
+    g = np.array([0.94, 0.02, 0.02, 0.02])
+    kappa = (abs(b[0] - b[1]) + abs(b[0] - b[2]) + abs(b[0] - b[3])) ** 2 / 9
+    w = g * (1 + kappa / (1e-8 * Wave ** 4 + Wave ** 2 * b))
+    np.testing.assert_allclose(r["omega"], w / w.sum(), rtol=1e-13)
+    assert r["omega"][0] < 0.5 * g[0]     # a visibly nonlinear case
+
+
+# ---------------------------------------------------------------- scale limiter fraction
+def test_limiter_fraction_is_the_largest_admissible_fraction():
+    """R18: the fraction pulls a point value toward the cell average just far
+    enough that density and pressure are >= eps.  Checked against the
+    definition on random segments: the state at f is admissible, the state a
+    little beyond f is not, and where the pressure bound is the active one
+    |p - eps| <= 1e-12 p_bar."""
+    rng = np.random.default_rng(23)
+    Wb_all = _random_euler_states(rng, 300)
+    active_p = 0
+    for Wb in Wb_all:
+        # a far-away point value, often with negative density or pressure
+        w = Wb + rng.normal(size=4) * np.array([1.0, 2.0, 2.0, 3.0]) * rng.uniform(0.2, 3.0)
+        pb = 0.4 * (Wb[3] - 0.5 * (Wb[1] ** 2 + Wb[2] ** 2) / Wb[0])
+        eps = min(1e-13, Wb[0], pb)
+        f = oracle.admissible_fraction(Wb, w, eps)
+        assert 0.0 <= f <= 1.0
+
+        def state(ff):
+            x = Wb + ff * (w - Wb)
+            return x[0], 0.4 * (x[3] - 0.5 * (x[1] ** 2 + x[2] ** 2) / x[0])
+        rho, p = state(f)
+        assert rho >= eps * (1 - 1e-12) and p >= eps - 1e-12 * pb, (rho, p, eps)
+        for ff in np.linspace(0, f, 7):
+            r_, p_ = state(ff)
+            assert r_ >= eps * (1 - 1e-12) and p_ >= eps - 1e-12 * pb
+        if f < 1.0:
+            r2, p2 = state(min(1.0, f * (1 + 1e-9) + 1e-12))
+            assert r2 < eps or p2 < eps
+            if abs(rho - eps) > 1e-12 * Wb[0]:      # the pressure bound is the active one
+                active_p += 1
+                assert abs(p - eps) <= 1e-12 * pb, (p, eps, pb)
+    assert active_p >= 50
