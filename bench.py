@@ -47,10 +47,17 @@ UNIT = "tri-updates/s"
 #   words, 10 geometry words and 4 index words; writes the state 3m words; in
 #   FP32 it also reads and writes the m compensation words of the averages.
 # Neighbour data are counted once (perfect reuse through the caches).
+#   k_fused (one kernel for the whole step) reads the cell state 3m words, the
+#   reconstruction and flux geometry 76 + 10 words, 4 index words and one slot
+#   word; writes the state 3m words; in FP32 it also reads and writes the m
+#   compensation words.  The edge-point records stay in shared memory.
 def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
+    comp = 2 * m * 4 if s == 4 else 0
     if kernel == "recon":
         return (3 * m + 76 + 18 * m) * s + 3 * 4
-    return (18 * m + m + 10 + 3 * m) * s + 4 * 4 + (2 * m * 4 if s == 4 else 0)
+    if kernel == "fused":
+        return (3 * m + 76 + 10 + 3 * m) * s + 4 * 4 + 4 + comp
+    return (18 * m + m + 10 + 3 * m) * s + 4 * 4 + comp
 
 
 # DRAM traffic per cell (bytes) measured with ncu (dram__bytes_read.sum +
@@ -238,7 +245,8 @@ def run_ours(args, rank, world, local_rank):
     precs = ("fp32", "fp64") if args.only == "both" else (args.only,)
     for prec in precs:
         K = args.steps if prec == "fp32" else max(3, args.steps // args.fp64_divisor)
-        s = hweno.Solver(hmesh, U0, eq="euler", precision=prec, time_rule=args.time_rule)
+        s = hweno.Solver(hmesh, U0, eq="euler", precision=prec, time_rule=args.time_rule,
+                         step_kernels=args.step_kernels)
         stream = s.stream
         for _ in range(args.warmup):
             s.step()
@@ -256,7 +264,8 @@ def run_ours(args, rank, world, local_rank):
         prof = s.profile_read()
         s.profile(False)
         flags = s.status_flags()
-        results[prec] = {"K": K, "ms": ms, "prof": prof, "clocks": clk.summary(), "flags": flags}
+        results[prec] = {"K": K, "ms": ms, "prof": prof, "clocks": clk.summary(), "flags": flags,
+                         "kernels": s.step_kernels()}
         if args.only == "both":
             # accuracy of the FP32 form against the FP64 form: the same fixed
             # steps from the initial state (outside the timed region)
@@ -295,8 +304,14 @@ def run_ours(args, rank, world, local_rank):
     value = replicas_value(N, K, r32["ms"], world)
     rec_ms = r32["prof"]["recon_ms"] / max(1, r32["prof"]["steps"])
     edge_ms = r32["prof"]["edge_ms"] / max(1, r32["prof"]["steps"])
-    dom = "recon" if rec_ms >= edge_ms else "edge"
-    dom_ms = max(rec_ms, edge_ms)
+    fused = r32["kernels"] == "fused"
+    if fused:
+        dom, dom_ms = "fused", rec_ms
+        kernel_ms = {"k_fused": rec_ms}
+    else:
+        dom = "recon" if rec_ms >= edge_ms else "edge"
+        dom_ms = max(rec_ms, edge_ms)
+        kernel_ms = {"k_recon": rec_ms, "k_edge": edge_ms}
     achieved = alg_bytes(dom, 4) * N / (dom_ms * 1e-3) / 1e9
     sha = kernel_sources_sha()
     tr = TRAFFIC["per_cell"].get(f"{dom}_fp32") if TRAFFIC["sources_sha"] == sha else None
@@ -333,10 +348,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind, "alg_bytes_per_cell": alg_bytes(dom, 4),
                      "traffic": (tr * N) if tr else None,
-                     "kernel_ms": {"k_recon": rec_ms, "k_edge": edge_ms}},
+                     "kernel_ms": kernel_ms, "step_kernels": r32["kernels"]},
         "e2e": {"value": replicas_value(N, e2e["steps"], e2e["s"] * 1e3, world), "unit": UNIT,
                 "h2d_bytes_per_step": e2e["bytes"], "d2h_bytes_per_step": e2e["bytes"]},
-        "gpu_launches": 2 * K,
+        "gpu_launches": (1 if fused else 2) * K,
         "clocks": r32["clocks"],
         "fp64": {"value": replicas_value(N, r64["K"], r64["ms"], world), "steps": r64["K"],
                  "ms_per_step": r64["ms"] / r64["K"], "kernel_ms": {"k_recon": rec64, "k_edge": edge64},
@@ -574,6 +589,8 @@ def main():
     ap.add_argument("--batch-fp64-solves", type=int, default=16,
                     help="solves of the batch re-run one by one in FP64 (accuracy and FP64 throughput)")
     ap.add_argument("--ref-cells", type=int, default=4000)
+    ap.add_argument("--step-kernels", default="default", choices=["default", "separate", "fused"],
+                    help="kernels of the single-solve step (default: fused in FP32, separate in FP64)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -56,7 +56,19 @@ typedef enum {
 
 typedef enum { HW_ADVECTION = 0, HW_BURGERS = 1, HW_EULER = 2 } hw_equation;
 typedef enum { HW_FP64 = 0, HW_FP32 = 1 } hw_precision;
-typedef enum { HW_BC_PERIODIC = 0, HW_BC_TRANSMISSIVE = 1 } hw_bc;
+/* Boundary conditions.  HW_BC_PERIODIC and HW_BC_TRANSMISSIVE are mesh-wide
+ * (hw_mesh_create); HW_BC_REFLECTIVE and HW_BC_INFLOW are set per boundary
+ * edge with hw_mesh_set_boundary (the walls and the inflow/outflow ends of the
+ * shock tubes of Section 3).  Every boundary edge has a ghost cell, the mirror
+ * image of its triangle, that joins the stencil (Section 2.2) and gives the
+ * exterior value of the flux:
+ *   transmissive (outflow): the triangle's own data; W^ext = W^int;
+ *   reflective (a wall; Euler, the scalar equations treat it as transmissive):
+ *     the mirrored solution, momentum reflected across the edge and the
+ *     derivative averages transformed accordingly; W^ext = the mirrored W^int;
+ *   inflow: the state hw_options.inflow with zero derivative averages;
+ *     W^ext = that state at every time node. */
+typedef enum { HW_BC_PERIODIC = 0, HW_BC_TRANSMISSIVE = 1, HW_BC_REFLECTIVE = 2, HW_BC_INFLOW = 3 } hw_bc;
 
 /* Solver options.  Defaults (hw_options_default): the paper's constants --
  * linear weights 0.94, 0.02, 0.02, 0.02 (Section 2.2, Step 3), epsilon 1e-8
@@ -76,13 +88,21 @@ typedef struct {
                            evaluation at t_{n+1}.  1 is for the single-solve step only: it
                            is refused with the scale limiter, by the batched form and by
                            the adjoint step (HW_EINVAL) */
-  int32_t reserved;     /* 0 */
+  int32_t step_kernels; /* kernels of a single-solve step: 0 = default = 1, a
+                           reconstruction kernel then a flux kernel with the edge-point
+                           data in the workspace; 2 = one fused reconstruct-and-flux
+                           kernel that keeps the edge-point data in shared memory and
+                           reconstructs each tile's halo itself (hw_state_init fails with
+                           HW_EINVAL if a tile of the mesh has more halo cells than the
+                           kernel holds).  Results agree to rounding. */
   double ax, ay;        /* advection velocity (HW_ADVECTION) */
   double gamma_gas;     /* ratio of specific heats (HW_EULER) */
   double cfl;           /* dt = cfl * min_K inradius_K / lambda_K */
   double gamma_lin[4];  /* linear weights gamma_1..gamma_4: each > 0 and sum 1 within
                            1e-12 (Section 2.2, Step 3); HW_EINVAL otherwise */
   double eps;           /* epsilon in the nonlinear weights, > 0 */
+  double inflow[4];     /* conservative state imposed at HW_BC_INFLOW edges (first m
+                           components used); default rho = 1, zero momentum, E = 2.5 */
 } hw_options;
 
 typedef struct hw_mesh hw_mesh;
@@ -110,6 +130,13 @@ hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, in
 hw_status hw_mesh_destroy(hw_mesh* mesh);
 /* Number of triangles. */
 int64_t hw_mesh_ntri(const hw_mesh* mesh);
+/* Boundary condition of every boundary edge: edge_bc[3*i + j] for local edge
+ * j of triangle i (caller's numbering), read only where that edge is on the
+ * boundary: HW_BC_TRANSMISSIVE, HW_BC_REFLECTIVE or HW_BC_INFLOW (see hw_bc).
+ * Host array.  Call before hw_state_init / hw_batch_create; a mesh starts
+ * with every boundary edge transmissive.  Errors: HW_EINVAL (null pointer, an
+ * invalid type on a boundary edge; the mesh is then unchanged). */
+hw_status hw_mesh_set_boundary(hw_mesh* mesh, const int32_t* edge_bc);
 /* Neighbour across local edge j (from vertex j to vertex j+1) of triangle i,
  * caller's numbering, -1 on a boundary: nbr[3*i + j].  nbe (optional, may be
  * NULL) receives the neighbour's local index of the same edge. Host arrays. */
@@ -164,9 +191,11 @@ hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps);
  * Enabling resets the accumulators. */
 hw_status hw_profile(hw_solver* s, int32_t enable);
 /* Synchronises on the recorded events; ms[0] = total reconstruction-kernel
- * time, ms[1] = total flux/update-kernel time (milliseconds) over nsteps
- * profiled steps. */
+ * time (the fused kernel's, when steps run it), ms[1] = total flux/update-kernel
+ * time (0 with the fused kernel), milliseconds over nsteps profiled steps. */
 hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps);
+/* Kernels the solver's steps run: *path = 2 (fused) or 1 (separate). */
+hw_status hw_step_kernels(const hw_solver* s, int32_t* path);
 hw_status hw_solver_destroy(hw_solver* s);
 
 /* Same as hw_step, but the scratch of the step (the edge-point buffer between
@@ -228,7 +257,8 @@ hw_status hw_step_keep(hw_solver* s, double dt, void* pb_out);
  * hw_adjoint_scratch_bytes(), 256-byte aligned.  Asynchronous on the stream.
  * Errors: HW_EINVAL (null pointer, a state or edge-point buffer not
  * 16-byte aligned, scratch not 256-byte aligned, dt <= 0, not the Euler
- * equations, scale limiter on), HW_ENOMEM (scratch_bytes too small). */
+ * equations, scale limiter on, walls or inflow edges on the mesh), HW_ENOMEM
+ * (scratch_bytes too small). */
 hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes);
 hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Pb_n, const void* Ubar_next,
                           void* Ubar_n, void* scratch, size_t scratch_bytes);

@@ -57,6 +57,8 @@ def lib():
         _lib.orc_lax_wendroff.argtypes = [ctypes.c_int, d, d, d, vp, vp]
         _lib.orc_cell_taylor.argtypes = [vp, vp, d, i64, vp]
         _lib.orc_flux_derivs.argtypes = [ctypes.c_int, d, d, d, vp, vp, vp, vp]
+        _lib.orc_set_boundary.argtypes = [vp, vp]
+        _lib.orc_set_inflow.argtypes = [vp, vp]
         _lib.orc_spectral_radius.argtypes = [ctypes.c_int, d, d, d, vp, d, d, vp]
         _lib.orc_admissible_fraction.argtypes = [d, vp, vp, d]
         _lib.orc_admissible_fraction.restype = d
@@ -78,7 +80,7 @@ class Oracle:
 
     def __init__(self, mesh, eq: str = "advection", a=(1.0, 1.0), gamma_gas: float = 1.4, cfl: float = 0.5,
                  gamma_lin=(0.94, 0.02, 0.02, 0.02), eps: float = 1e-8, linear_only: bool = False,
-                 positivity: bool = False, time_rule: str = "lobatto"):
+                 positivity: bool = False, time_rule: str = "lobatto", inflow=None):
         L = lib()
         self.mesh = mesh
         self.eq = EQ[eq]
@@ -93,7 +95,14 @@ class Oracle:
                             ctypes.byref(h)))
         self._h = h
         if positivity:
-            _check(L.orc_set_positivity(h, 1))
+            # True: scale limiter + flux blending; "scale_only": the scale limiter alone
+            _check(L.orc_set_positivity(h, 2 if positivity == "scale_only" else 1))
+        if getattr(mesh, "edge_bc", None) is not None:
+            self._ebc = np.ascontiguousarray(mesh.edge_bc, dtype=np.int32)
+            _check(L.orc_set_boundary(h, _ptr(self._ebc)))
+        if inflow is not None:
+            self._win = np.ascontiguousarray(inflow, dtype=np.float64)
+            _check(L.orc_set_inflow(h, _ptr(self._win)))
         if time_rule != "lobatto":
             _check(L.orc_set_time_rule(h, {"gauss": 1}[time_rule]))
         self.a = a

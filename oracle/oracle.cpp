@@ -43,6 +43,15 @@
 //   R13 non-periodic boundaries are transmissive: the ghost cell is the mirror
 //       image of the cell with the cell's own data, and W^ext = W^int on the
 //       boundary edge;
+//   R25 reflective and inflow boundaries (the walls and the inflow/outflow
+//       ends of Section 3's shock tubes): the ghost is the same mirror image
+//       of the cell; at a wall it carries the mirrored solution (momentum
+//       reflected, derivative averages by the chain rule) and W^ext is the
+//       mirrored interior value; at an inflow edge it carries the imposed
+//       state with zero derivative averages and W^ext is that state;
+//       outflow is transmissive;
+//   R23 (with the scale limiter) each edge flux blended with the first-order
+//       LLF flux of the two averages so that the new averages stay admissible;
 //   R22 (option) the time rule of Eq. flux as two-node Gauss-Legendre, nodes
 //       dt (1/2 -+ sqrt(3)/6), weights 1/2, with the central values of Eq.
 //       timeflux from a separate Taylor evaluation at t_{n+1};
@@ -113,7 +122,7 @@ template <class S> HD<S> operator/(HD<S> x, HD<S> y) { return x * recip(y); }
 
 // ------------------------------------------------------------------ problem
 enum { EQ_ADVECTION = 0, EQ_BURGERS = 1, EQ_EULER = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3 };
 
 struct Params {
   int eq;
@@ -142,11 +151,13 @@ struct Problem {
   double Lx = 0, Ly = 0;
   int bc = BC_PERIODIC;
   std::vector<double> vx, vy;          // unwrapped vertices [nt][3]
-  std::vector<double> area, cx, cy, inr;
+  std::vector<double> area, cx, cy, inr, perim;
   std::vector<std::array<int32_t, 3>> nbr;   // neighbour across local edge j (-1: boundary)
   std::vector<std::array<int32_t, 3>> nbe;   // neighbour's local edge index
   std::vector<std::array<double, 6>> nbshift;  // (sx, sy) per local edge: nb frame + shift = own frame
   std::vector<EdgeRec> edges;
+  std::vector<std::array<int, 3>> ebc;       // type of each boundary edge (R13, R25)
+  double win[4] = {1.0, 0.0, 0.0, 2.5};      // state imposed at inflow edges (conservative)
   std::string err;
 };
 
@@ -201,7 +212,7 @@ bool build_connectivity(Problem& pb, const int32_t* tri) {
 bool build_geometry(Problem& pb, const double* xy, const int32_t* tri) {
   const int64_t nt = pb.nt;
   pb.vx.resize(3 * nt); pb.vy.resize(3 * nt);
-  pb.area.resize(nt); pb.cx.resize(nt); pb.cy.resize(nt); pb.inr.resize(nt);
+  pb.area.resize(nt); pb.cx.resize(nt); pb.cy.resize(nt); pb.inr.resize(nt); pb.perim.resize(nt);
   for (int64_t t = 0; t < nt; ++t) {
     double x0 = xy[2 * tri[3 * t]], y0 = xy[2 * tri[3 * t] + 1];
     for (int v = 0; v < 3; ++v) {
@@ -218,8 +229,10 @@ bool build_geometry(Problem& pb, const double* xy, const int32_t* tri) {
     double per = 0;
     for (int j = 0; j < 3; ++j) per += std::hypot(X[(j + 1) % 3] - X[j], Y[(j + 1) % 3] - Y[j]);
     pb.inr[t] = 2.0 * a / per;
+    pb.perim[t] = per;
   }
   // periodic shift of each neighbour and the edge list (one record per edge)
+  pb.ebc.assign(nt, {BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE});
   pb.nbshift.assign(nt, {0, 0, 0, 0, 0, 0});
   pb.edges.clear();
   for (int64_t t = 0; t < nt; ++t) {
@@ -364,6 +377,56 @@ void stencil_member(const Problem& pb, int64_t t, int l, double X[3], double Y[3
   }
 }
 
+// Unit normal of local edge j of cell t, outward of t.
+void edge_normal(const Problem& pb, int64_t t, int j, double& nx, double& ny) {
+  const double Ax = pb.vx[3 * t + j], Ay = pb.vy[3 * t + j];
+  const double Bx = pb.vx[3 * t + (j + 1) % 3], By = pb.vy[3 * t + (j + 1) % 3];
+  const double len = std::hypot(Bx - Ax, By - Ay);
+  nx = (By - Ay) / len; ny = -(Bx - Ax) / len;
+}
+
+// Mirror of an Euler state across a wall with unit normal n: density and
+// energy kept, momentum reflected, m -> m - 2 (m . n) n.
+template <class S> void mirror_state(double nx, double ny, const S* W, S* Wm) {
+  const S mn = W[1] * S(nx) + W[2] * S(ny);
+  Wm[0] = W[0];
+  Wm[1] = W[1] - S(2.0 * nx) * mn;
+  Wm[2] = W[2] - S(2.0 * ny) * mn;
+  Wm[3] = W[3];
+}
+
+// Data carried by the ghost across boundary edge j of cell t, all components
+// (R13, R25).  The ghost is the mirror image of t across the edge.
+//   transmissive: t's own averages;
+//   reflective (Euler; the scalar equations treat it as transmissive): the
+//     mirrored solution W_g(x) = M W(Rx), R the reflection across the edge
+//     line and M the state mirror above, so that Wbar_g = M Wbar and the
+//     averages of the gradient follow the chain rule, grad W_g = M (grad W) R;
+//   inflow: the imposed state, with zero derivative averages.
+template <class S> void ghost_data(const Problem& pb, const S* U, int64_t t, int j, S W[4], S V[4], S Y[4]) {
+  const int m = pb.P.m;
+  const int type = pb.ebc[t][j];
+  if (type == BC_INFLOW) {
+    for (int c = 0; c < m; ++c) { W[c] = S(pb.win[c]); V[c] = S(0.0); Y[c] = S(0.0); }
+    return;
+  }
+  for (int c = 0; c < m; ++c) { W[c] = Uat(U, pb, 0, c, t); V[c] = Uat(U, pb, 1, c, t); Y[c] = Uat(U, pb, 2, c, t); }
+  if (type != BC_REFLECTIVE || pb.P.eq != EQ_EULER) return;
+  double nx, ny;
+  edge_normal(pb, t, j, nx, ny);
+  S Wm[4], Vm[4], Ym[4];
+  mirror_state(nx, ny, W, Wm);
+  mirror_state(nx, ny, V, Vm);   // the state mirror applied to the x- and y-derivative averages
+  mirror_state(nx, ny, Y, Ym);
+  // then the reflection R = I - 2 n n^T acting on (d/dx, d/dy) of every component
+  for (int c = 0; c < 4; ++c) {
+    const S dn = Vm[c] * S(nx) + Ym[c] * S(ny);
+    V[c] = Vm[c] - S(2.0 * nx) * dn;
+    Y[c] = Ym[c] - S(2.0 * ny) * dn;
+    W[c] = Wm[c];
+  }
+}
+
 // Steps 1-5 of Section 2.2 for component c of cell t.
 template <class S> CellRecon<S> reconstruct(const Problem& pb, const S* U, int64_t t, int c) {
   CellRecon<S> R;
@@ -389,7 +452,13 @@ template <class S> CellRecon<S> reconstruct(const Problem& pb, const S* U, int64
     stencil_member(pb, t, l, X, Y, a, src);
     for (int v = 0; v < 3; ++v) { Xs[l][v] = (X[v] - x0) / h0; Ys[l][v] = (Y[v] - y0) / h0; }
     As[l] = a;
-    Wb[l] = Uat(U, pb, 0, c, src); Vb[l] = Uat(U, pb, 1, c, src); Yb[l] = Uat(U, pb, 2, c, src);
+    if (pb.nbr[t][l - 1] >= 0) {
+      Wb[l] = Uat(U, pb, 0, c, src); Vb[l] = Uat(U, pb, 1, c, src); Yb[l] = Uat(U, pb, 2, c, src);
+    } else {
+      S gw[4], gv[4], gy[4];
+      ghost_data(pb, U, t, l - 1, gw, gv, gy);
+      Wb[l] = gw[c]; Vb[l] = gv[c]; Yb[l] = gy[c];
+    }
   }
   double mean[4][6];
   for (int l = 0; l < 4; ++l) basis_means(Xs[l], Ys[l], M3, M4, M5, mean[l]);
@@ -748,6 +817,53 @@ template <class S> void positivity_time_scaling(const Problem& pb, CellRecon<S>*
   for (int c = 0; c < 4; ++c) rec[c].theta_t = th;
 }
 
+// Positivity-preserving flux blending (R23, with the scale limiter, Euler).
+// The scale limiter keeps the point values admissible, but a one-step (ADER)
+// update built from time-Taylor values is not a convex combination of them, so
+// the new cell averages can still lose positivity.  Following Hu, Adams and
+// Shu (2013), each cell average is written as
+//   Wbar^{n+1} = sum_e (|e| / P) Phi_e,
+//   Phi_e = Wbar - (dt P / |K|) (Fhat_e - F(Wbar) . n_e)
+// (P the perimeter; sum_e |e| n_e = 0), and the edge flux is replaced by
+// Fhat = FL + theta (FH - FL), FL the first-order local Lax-Friedrichs flux of
+// the two cell averages (WL, WR; on a boundary WR is the ghost's) with the same alpha, theta in [0, 1] the largest value
+// that keeps Phi_e admissible on both sides of the edge (the scale limiter's
+// fraction along the segment from Phi_e(0) to Phi_e(1)).  Both sides use the
+// same theta, so the update stays conservative.  Fe is the high-order edge
+// flux times |e| on entry and the blended one on exit.
+template <class S>
+void flux_blend(const Problem& pb, const S* WL, const S* WR, const EdgeRec& e, S alpha, double dt, S Fe[4]) {
+  const double gam = pb.P.gam;
+  S HL[4], HR[4], FL[4], FH[4];
+  flux_normal(pb.P, WL, e.nx, e.ny, HL);
+  flux_normal(pb.P, WR, e.nx, e.ny, HR);
+  for (int c = 0; c < 4; ++c) {
+    FL[c] = S(0.5) * (HL[c] + HR[c] - alpha * (WR[c] - WL[c]));
+    FH[c] = Fe[c] / S(e.len);
+  }
+  S theta = S(1.0);
+  for (int side = 0; side < (e.R >= 0 ? 2 : 1); ++side) {
+    const int64_t k = side == 0 ? e.L : e.R;
+    const S* Wk = side == 0 ? WL : WR;
+    const S* Hk = side == 0 ? HL : HR;
+    const double sg = side == 0 ? 1.0 : -1.0;   // the edge normal is outward for L, inward for R
+    const S pk = pressure(gam, Wk);
+    if (!(val(Wk[0]) > 0) || !(val(pk) > 0)) continue;   // the average itself is not admissible
+    const double eps = std::min(1e-13, std::min(val(Wk[0]), val(pk)));
+    const S lam = S(sg * dt * pb.perim[k] / pb.area[k]);
+    S phi0[4], phi1[4];
+    for (int c = 0; c < 4; ++c) {
+      phi0[c] = Wk[c] - lam * (FL[c] - Hk[c]);
+      phi1[c] = Wk[c] - lam * (FH[c] - Hk[c]);
+    }
+    S th = S(0.0);
+    if (val(phi0[0]) >= eps && val(pressure(gam, phi0)) >= eps) th = admissible_fraction(gam, phi0, phi1, eps);
+    if (val(th) < val(theta)) theta = th;
+  }
+  if (val(theta) < 1.0)
+    for (int c = 0; c < 4; ++c) Fe[c] = S(e.len) * (FL[c] + theta * (FH[c] - FL[c]));
+}
+
 // One time step.  If `mask` is non-null only cells with mask[i] != 0 are
 // updated (their stencils are reconstructed as needed); other entries of Unew
 // are copied from U.
@@ -792,6 +908,10 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
       WL[c] = Uat(U, pb, 0, c, e.L);
       WR[c] = Uat(U, pb, 0, c, e.R >= 0 ? e.R : e.L);
     }
+    if (e.R < 0) {   // the ghost's average (R13, R25)
+      S gv[4], gy[4];
+      ghost_data(pb, U, e.L, e.jL, WR, gv, gy);
+    }
     S alpha = smax(spectral_radius_n(pb.P, WL, e.nx, e.ny), spectral_radius_n(pb.P, WR, e.nx, e.ny));
     for (int gi = 0; gi < 2; ++gi) {
       double s = (gi == 0) ? 0.5 - kGL : 0.5 + kGL;
@@ -801,7 +921,17 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
       if (e.R >= 0) {
         side_taylor(pb, rec.data() + slot[e.R] * m, x - e.sx, y - e.sy, We, Wte, Wtte);
       } else {
-        for (int c = 0; c < m; ++c) { We[c] = Wi[c]; Wte[c] = Wti[c]; Wtte[c] = Wtti[c]; }
+        // boundary: the ghost's Taylor data at the edge point (R13, R25)
+        const int type = pb.ebc[e.L][e.jL];
+        if (type == BC_INFLOW) {
+          for (int c = 0; c < m; ++c) { We[c] = S(pb.win[c]); Wte[c] = S(0.0); Wtte[c] = S(0.0); }
+        } else if (type == BC_REFLECTIVE && pb.P.eq == EQ_EULER) {
+          mirror_state(e.nx, e.ny, Wi, We);      // the mirrored solution at a point of the wall
+          mirror_state(e.nx, e.ny, Wti, Wte);
+          mirror_state(e.nx, e.ny, Wtti, Wtte);
+        } else {
+          for (int c = 0; c < m; ++c) { We[c] = Wi[c]; Wte[c] = Wti[c]; Wtte[c] = Wtti[c]; }
+        }
       }
       // Eqs. tay / tayext at the time nodes, LLF flux, time quadrature (Eq. flux)
       const bool gauss = pb.P.time_rule == 1;
@@ -833,6 +963,7 @@ template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Un
         }
       }
     }
+    if (pb.P.positivity == 1 && pb.P.eq == EQ_EULER) flux_blend(pb, WL, WR, e, alpha, dt, Fe);
     for (int c = 0; c < m; ++c) {
       Rf[e.L * m + c] = Rf[e.L * m + c] + Fe[c];
       GV[e.L * m + c] = GV[e.L * m + c] + Se[c] * S(e.nx);
@@ -900,9 +1031,32 @@ int orc_create(const double* xy, int64_t nv, const int32_t* tri, int64_t nt, dou
 
 void orc_destroy(orc_problem* p) { delete reinterpret_cast<Problem*>(p); }
 
-// Switch the scale limiter (R18) on or off.
+// Positivity: 0 off; 1 the scale limiter (R18) with the flux blending (R23);
+// 2 the scale limiter alone (the literal reading of Section 3, for tests).
 int orc_set_positivity(orc_problem* p, int on) {
+  if (on < 0 || on > 2) { g_err = "positivity must be 0, 1 or 2"; return 1; }
   reinterpret_cast<Problem*>(p)->P.positivity = on;
+  return 0;
+}
+
+// Boundary types (R13, R25): edge_bc[3 t + j] for local edge j of cell t, read
+// where the edge is on the boundary: 1 transmissive, 2 reflective, 3 inflow.
+int orc_set_boundary(orc_problem* p, const int32_t* edge_bc) {
+  Problem* pb = reinterpret_cast<Problem*>(p);
+  for (int64_t t = 0; t < pb->nt; ++t)
+    for (int j = 0; j < 3; ++j) {
+      if (pb->nbr[t][j] >= 0) continue;
+      const int b = edge_bc[3 * t + j];
+      if (b < BC_TRANSMISSIVE || b > BC_INFLOW) { g_err = "boundary type must be 1, 2 or 3"; return 1; }
+      pb->ebc[t][j] = b;
+    }
+  return 0;
+}
+
+// The state imposed at inflow edges (conservative variables, m values).
+int orc_set_inflow(orc_problem* p, const double* W) {
+  Problem* pb = reinterpret_cast<Problem*>(p);
+  for (int c = 0; c < pb->P.m; ++c) pb->win[c] = W[c];
   return 0;
 }
 

@@ -47,7 +47,7 @@ template <int n> __device__ __forceinline__ void cp_async_wait() {
 
 // One tile's inputs, staged ahead of use.
 template <typename R> struct AdjIn {
-  R geo[NRGEO][kAdjCells];          // all geometry planes
+  R geo[kStepPlanes][kAdjCells];    // the geometry planes of the step
   R pb[kAdjCells][18 * kM];         // own edge-point Taylor records; later the contribution tile [cell][4][3m]
   R us[4][kAdjCells][3 * kM];       // state records: 0 = the cell, 1 + j = neighbour j
   R ub[4][kAdjCells][3 * kM];       // cotangent-of-U^{n+1} records, same slots
@@ -82,7 +82,7 @@ struct AdjPtrs {
 template <typename R> __device__ __forceinline__ void issue_base(AdjIn<R>& B, const AdjPtrs& a, int cell0, int t) {
   constexpr int m = kM, rec = 3 * m, prec = 18 * m, cpr = (int)sizeof(R) * kAdjCells / 16;   // chunks per plane row
   const R* rg = static_cast<const R*>(a.rg);
-  for (int k = t; k < NRGEO * cpr; k += kAdjThreads) {
+  for (int k = t; k < kStepPlanes * cpr; k += kAdjThreads) {
     const int p = k / cpr, q = k % cpr;
     cp_async16(reinterpret_cast<char*>(&B.geo[p][0]) + 16 * q,
                reinterpret_cast<const char*>(rg + (size_t)p * a.ld + cell0) + 16 * q);

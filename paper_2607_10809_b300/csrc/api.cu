@@ -3,6 +3,7 @@
 // steps, and run_to through a captured CUDA graph of several steps.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,8 +36,12 @@ constexpr int kGraphSteps = 16;  // steps per captured graph (even: the state pa
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t rgeo, igeo, U0, U1, Pb, comp, comp_bytes, area, perm, stage, sc, partial, consv, total;
+  size_t rgeo, igeo, U0, U1, Pb, comp, comp_bytes, area, perm, stage, sc, partial, consv, fslot, fhoff, fhalo, total;
 };
+
+// Tile shape of the fused step in a precision.
+int fused_tile(int prec) { return prec == HW_FP32 ? kFusedTile32 : kFusedTile64; }
+int fused_halo_cap(int prec) { return prec == HW_FP32 ? kFusedHalo32 : kFusedHalo64; }
 
 Layout make_layout(int64_t N, int m, int prec) {
   const size_t s = prec == HW_FP64 ? 8 : 4;
@@ -58,8 +63,53 @@ Layout make_layout(int64_t N, int m, int prec) {
   L.sc = take(sizeof(DevScalars));
   L.partial = take((size_t)kConsvBlocks * 4 * 8);
   L.consv = take(4 * 8);
+  // tables of the fused step: neighbour slots per cell, halo offsets and cells per tile
+  const size_t ntiles = (size_t)((N + fused_tile(prec) - 1) / fused_tile(prec));
+  L.fslot = take(ld * 4);
+  L.fhoff = take((ntiles + 1) * 4);
+  L.fhalo = take(ntiles * (size_t)fused_halo_cap(prec) * 4);
   L.total = o;
   return L;
+}
+
+// Tables of the fused step for tiles of TT consecutive internal cells: the
+// halo of each tile (cells outside it that share an edge with one of its
+// cells, ascending) and per cell the packed slots of its three neighbours.
+// Returns false (tables unusable) if a tile's halo exceeds HC cells.
+bool build_fused_tables(const HostMesh& M, int TT, int HC, std::vector<int32_t>& slot, std::vector<int32_t>& off,
+                        std::vector<int32_t>& halo) {
+  const int64_t nt = M.nt, ntiles = (nt + TT - 1) / TT;
+  slot.assign((size_t)nt, 0);
+  off.assign((size_t)ntiles + 1, 0);
+  halo.clear();
+  std::vector<int32_t> loc;
+  for (int64_t b = 0; b < ntiles; ++b) {
+    const int64_t c0 = b * TT, c1 = std::min<int64_t>(nt, c0 + TT);
+    loc.clear();
+    for (int64_t k = c0; k < c1; ++k)
+      for (int j = 0; j < 3; ++j) {
+        const int32_t u = M.igeo[(size_t)(I_NBR + j) * nt + k];
+        if (u >= 0 && (u < c0 || u >= c1)) loc.push_back(u);
+      }
+    std::sort(loc.begin(), loc.end());
+    loc.erase(std::unique(loc.begin(), loc.end()), loc.end());
+    if ((int)loc.size() > HC) return false;
+    off[(size_t)b] = (int32_t)halo.size();
+    halo.insert(halo.end(), loc.begin(), loc.end());
+    for (int64_t k = c0; k < c1; ++k) {
+      int32_t packed = 0;
+      for (int j = 0; j < 3; ++j) {
+        const int32_t u = M.igeo[(size_t)(I_NBR + j) * nt + k];
+        int v = kSlotNone;
+        if (u >= c0 && u < c1) v = (int)(u - c0);
+        else if (u >= 0) v = TT + (int)(std::lower_bound(loc.begin(), loc.end(), u) - loc.begin());
+        packed |= v << (kSlotBits * j);
+      }
+      slot[(size_t)k] = packed;
+    }
+  }
+  off[(size_t)ntiles] = (int32_t)halo.size();
+  return true;
 }
 
 int ncomp(int eq) { return eq == HW_EULER ? 4 : 1; }
@@ -81,6 +131,7 @@ hw_status check_options(const hw_options* o) {
   if (o->time_rule != 0 && o->time_rule != 1) return fail(HW_EINVAL, "time_rule must be 0 or 1");
   if (o->time_rule == 1 && o->positivity)
     return fail(HW_EINVAL, "the Gauss-Legendre time rule is not combined with the scale limiter");
+  if (o->step_kernels < 0 || o->step_kernels > 2) return fail(HW_EINVAL, "step_kernels must be 0, 1 or 2");
   return HW_OK;
 }
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -131,6 +182,7 @@ hw_status hw_encode_plane_maps(TensorMaps* maps, int precision, char* rgeo, char
   hw_status st = encode_planes(&maps->geo, dt, es, rgeo, N, kReconPlanes, ld);
   if (st == HW_OK) st = encode_planes(&maps->egeo, dt, es, rgeo + (size_t)G_NRM * (size_t)ld * es, N, kEdgePlanes, ld);
   if (st == HW_OK) st = encode_planes(&maps->idx, CU_TENSOR_MAP_DATA_TYPE_INT32, 4, igeo, N, NIGEO, ld);
+  if (st == HW_OK) st = encode_planes(&maps->lgeo, dt, es, rgeo + (size_t)G_PK * (size_t)ld * es, N, kLimPlanes, ld);
   return st;
 }
 
@@ -143,6 +195,9 @@ struct hw_solver {
   char* ws = nullptr;
   Layout L{};
   int cur = 0;  // index of the current state buffer
+  bool special_bc = false;   // the mesh has walls or inflow edges
+  bool fused = false;        // steps run the fused reconstruct-and-flux kernel
+  int fused_ntiles = 0;      // tiles of the fused step (0: tables not available)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -178,9 +233,16 @@ struct hw_solver {
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
     a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
     a.P.time_rule = opt.time_rule;
-    for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
+    for (int l = 0; l < 4; ++l) { a.P.g[l] = opt.gamma_lin[l]; a.P.win[l] = opt.inflow[l]; }
     eq_params_finish(a.P);
+    a.fused = FusedTiles{reinterpret_cast<const int32_t*>(ws + L.fslot), reinterpret_cast<const int32_t*>(ws + L.fhoff),
+                         reinterpret_cast<const int32_t*>(ws + L.fhalo), fused_ntiles};
     return a;
+  }
+  // one step on stream st: the fused kernel, or reconstruction then flux
+  void launch(const StepArgs& a, cudaStream_t st) {
+    if (fused) launch_fused(prec, eq, a, st);
+    else launch_step(prec, eq, a, st);
   }
 };
 
@@ -197,6 +259,7 @@ void hw_options_default(hw_options* o) {
   o->cfl = 0.5;
   o->gamma_lin[0] = 0.94; o->gamma_lin[1] = 0.02; o->gamma_lin[2] = 0.02; o->gamma_lin[3] = 0.02;
   o->eps = 1e-8;
+  o->inflow[0] = 1.0; o->inflow[3] = 2.5;   // rest state, rho = 1, p = 1 (gamma 1.4)
 }
 
 hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, int64_t ntri, double Lx, double Ly,
@@ -212,6 +275,32 @@ hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, in
     return fail(inval ? HW_EINVAL : HW_EMESH, err);
   }
   *out = h;
+  return HW_OK;
+}
+
+hw_status hw_mesh_set_boundary(hw_mesh* mesh, const int32_t* edge_bc) {
+  if (!mesh || !edge_bc) return fail(HW_EINVAL, "null pointer");
+  HostMesh& M = mesh->M;
+  const int64_t nt = M.nt;
+  for (int64_t t = 0; t < nt; ++t)
+    for (int j = 0; j < 3; ++j)
+      if (M.nbr_orig[3 * t + j] < 0) {
+        const int b = edge_bc[3 * t + j];
+        if (b != HW_BC_TRANSMISSIVE && b != HW_BC_REFLECTIVE && b != HW_BC_INFLOW)
+          return fail(HW_EINVAL, "boundary edges take HW_BC_TRANSMISSIVE, HW_BC_REFLECTIVE or HW_BC_INFLOW");
+      }
+  bool special = false;
+  for (int64_t t = 0; t < nt; ++t) {
+    int32_t& packed = M.igeo[(size_t)I_NBE * nt + M.inv[t]];
+    for (int j = 0; j < 3; ++j) {
+      packed &= ~(3 << (9 + 2 * j));
+      if (M.nbr_orig[3 * t + j] >= 0) continue;
+      const int code = edge_bc[3 * t + j] - HW_BC_TRANSMISSIVE;   // 0 transmissive, 1 wall, 2 inflow
+      packed |= code << (9 + 2 * j);
+      special = special || code != 0;
+    }
+  }
+  M.special_bc = special;
   return HW_OK;
 }
 
@@ -274,6 +363,7 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
   s->m = ncomp(opt->eq);
   s->N = M.nt;
   s->ld = padded_cells(M.nt);
+  s->special_bc = M.special_bc;
   s->L = make_layout(M.nt, s->m, precision);
   if (workspace_bytes < s->L.total) { delete s; return fail(HW_ENOMEM, "workspace smaller than hw_workspace_bytes"); }
   s->ws = static_cast<char*>(workspace);
@@ -308,6 +398,25 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
   if (hw_status st = hw_encode_plane_maps(&s->maps, precision, s->ws + s->L.rgeo, s->ws + s->L.igeo, M.nt, s->ld))
     return bail(st);
   prepare_step_kernels(precision, s->eq);
+  // fused step (step_kernels 2): tables for tiles of fused_tile(precision) cells
+  {
+    std::vector<int32_t> slot, off, halo;
+    const bool ok = build_fused_tables(M, fused_tile(precision), fused_halo_cap(precision), slot, off, halo);
+    if (s->opt.step_kernels == 2 && !ok)
+      return bail(fail(HW_EINVAL, "the fused step needs every tile's halo to fit its capacity; use step_kernels 1"));
+    if (ok) {
+      e = cudaMemcpyAsync(s->ws + s->L.fslot, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->ws + s->L.fhoff, off.data(), off.size() * 4, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess && !halo.empty())
+        e = cudaMemcpyAsync(s->ws + s->L.fhalo, halo.data(), halo.size() * 4, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);   // the host tables go out of scope
+      if (e != cudaSuccess) return bail(fail(HW_ECUDA, std::string("fused tables: ") + cudaGetErrorString(e)));
+      s->fused_ntiles = (int)(off.size() - 1);
+      s->fused = s->opt.step_kernels == 2;
+      if (s->fused) prepare_fused_kernel(precision, s->eq);
+    }
+  }
   // Look up the static scratch array of hw_step_static_scratch on this device
   // now: the lookup loads the module that holds the array, which commits its
   // memory, so that a later step without caller scratch allocates nothing.
@@ -334,13 +443,18 @@ hw_status hw_step(hw_solver* s, double dt) {
   if (s->profiling && s->nprof < kMaxProfiledSteps) {
     cudaEvent_t* e = &s->ev[3 * s->nprof];
     HW_CUDA(cudaEventRecord(e[0], s->stream));
-    launch_recon(s->prec, s->eq, a, s->stream);
-    HW_CUDA(cudaEventRecord(e[1], s->stream));
-    launch_edge(s->prec, s->eq, a, s->stream);
+    if (s->fused) {
+      launch_fused(s->prec, s->eq, a, s->stream);
+      HW_CUDA(cudaEventRecord(e[1], s->stream));
+    } else {
+      launch_recon(s->prec, s->eq, a, s->stream);
+      HW_CUDA(cudaEventRecord(e[1], s->stream));
+      launch_edge(s->prec, s->eq, a, s->stream);
+    }
     HW_CUDA(cudaEventRecord(e[2], s->stream));
     ++s->nprof;
   } else {
-    launch_step(s->prec, s->eq, a, s->stream);
+    s->launch(a, s->stream);
   }
   HW_CUDA(cudaGetLastError());
   s->cur = 1 - s->cur;
@@ -353,7 +467,7 @@ static hw_status ensure_graph(hw_solver* s, int parity) {
   HW_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
   int cur = parity;
   for (int k = 0; k < kGraphSteps; ++k) {
-    launch_step(s->prec, s->eq, s->args(cur, 0.0), s->cap_stream);
+    s->launch(s->args(cur, 0.0), s->cap_stream);
     cur = 1 - cur;
   }
   cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
@@ -460,6 +574,12 @@ hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps) {
     ms[1] += b;
   }
   if (nsteps) *nsteps = s->nprof;
+  return HW_OK;
+}
+
+hw_status hw_step_kernels(const hw_solver* s, int32_t* path) {
+  if (!s || !path) return fail(HW_EINVAL, "null pointer");
+  *path = s->fused ? 2 : 1;
   return HW_OK;
 }
 
@@ -637,6 +757,7 @@ hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* 
   if (s->eq != HW_EULER) return fail(HW_EINVAL, "the adjoint step is implemented for the Euler equations");
   if (s->opt.positivity) return fail(HW_EINVAL, "the adjoint step does not cover the scale limiter");
   if (s->opt.time_rule != 0) return fail(HW_EINVAL, "the adjoint step follows the Gauss-Lobatto time rule only");
+  if (s->special_bc) return fail(HW_EINVAL, "the adjoint step covers periodic and transmissive boundaries only");
   if (!(dt > 0)) return fail(HW_EINVAL, "the adjoint step needs the (fixed) time step dt > 0");
   if ((reinterpret_cast<uintptr_t>(U_n) | reinterpret_cast<uintptr_t>(Pb_n) | reinterpret_cast<uintptr_t>(Ubar_next) |
        reinterpret_cast<uintptr_t>(Ubar_n)) % 16)

@@ -129,7 +129,7 @@ struct hw_batch {
     const int bps = std::max(1, std::min(sched.blocks_per_sm > 0 ? sched.blocks_per_sm : per_sm, per_sm));
     a.grid = std::max(1, std::min(bps * sms, plan.ntiles));
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
-    for (int l = 0; l < 4; ++l) a.P.g[l] = opt.gamma_lin[l];
+    for (int l = 0; l < 4; ++l) { a.P.g[l] = opt.gamma_lin[l]; a.P.win[l] = opt.inflow[l]; }
     eq_params_finish(a.P);
     a.P.positivity = (opt.eq == HW_EULER && opt.positivity) ? 1 : 0;
     a.P.time_rule = 0;

@@ -34,8 +34,9 @@ struct EqParams {
   // constant rounded once to float for the single-precision kernels (a
   // conversion or a double operation inside a kernel runs on the slow
   // double-precision pipe)
+  double win[4];    // state imposed at inflow boundary edges (conservative)
   double gm1, amag;
-  float axf, ayf, gamf, gm1f, epsf, amagf, gf[4];
+  float axf, ayf, gamf, gm1f, epsf, amagf, gf[4], winf[4];
 };
 
 inline void eq_params_finish(EqParams& P) {
@@ -43,7 +44,7 @@ inline void eq_params_finish(EqParams& P) {
   P.amag = std::sqrt(P.ax * P.ax + P.ay * P.ay);
   P.axf = (float)P.ax; P.ayf = (float)P.ay; P.gamf = (float)P.gam; P.gm1f = (float)P.gm1;
   P.epsf = (float)P.eps; P.amagf = (float)P.amag;
-  for (int l = 0; l < 4; ++l) P.gf[l] = (float)P.g[l];
+  for (int l = 0; l < 4; ++l) { P.gf[l] = (float)P.g[l]; P.winf[l] = (float)P.win[l]; }
 }
 
 // 1 / x correctly rounded (the same value as the IEEE division 1 / x)
@@ -59,7 +60,9 @@ template <typename R> struct EqC {
   static __device__ __forceinline__ R eps(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.eps; else return P.epsf; }
   static __device__ __forceinline__ R amag(const EqParams& P) { if constexpr (sizeof(R) == 8) return P.amag; else return P.amagf; }
   static __device__ __forceinline__ R g(const EqParams& P, int l) { if constexpr (sizeof(R) == 8) return P.g[l]; else return P.gf[l]; }
+  static __device__ __forceinline__ R win(const EqParams& P, int c) { if constexpr (sizeof(R) == 8) return P.win[c]; else return P.winf[c]; }
 };
+
 
 template <typename R> struct GeoView {
   const R* __restrict__ rg;        // [NRGEO][ld]
@@ -72,6 +75,48 @@ template <typename R> struct GeoView {
 
 constexpr int kEqAdvection = 0, kEqBurgers = 1, kEqEuler = 2;
 template <int EQ> struct EqTraits { static constexpr int m = (EQ == kEqEuler) ? 4 : 1; };
+
+// ---------------------------------------------------------------- boundary ghosts
+// Type of the ghost across local edge j (bits 9 + 2j of the packed edge plane):
+// transmissive (the cell's own data), a reflective wall (the mirrored
+// solution; Euler, the scalar equations treat it as transmissive) or an inflow
+// edge (the imposed state, flat).
+constexpr int kGhostTransmissive = 0, kGhostWall = 1, kGhostInflow = 2;
+__device__ __forceinline__ int ghost_type(int packed, int j) { return (packed >> (9 + 2 * j)) & 3; }
+
+// Component c of the mirror of a 4-vector of Euler quantities across a wall
+// with unit normal n: momentum reflected, m -> m - 2 (m . n) n.
+template <typename R> __device__ __forceinline__ R mirror_c(R nx, R ny, const R* X, int c) {
+  if (c == 1 || c == 2) {
+    const R xn = X[1] * nx + X[2] * ny;
+    return X[c] - R(2) * (c == 1 ? nx : ny) * xn;
+  }
+  return X[c];
+}
+
+// Component c of the averages (W, W_x, W_y) carried by the ghost across a
+// boundary edge with outward unit normal n; own: the cell's state record.
+// Wall: W_g(x) = M W(Rx) with M the state mirror and R the reflection across
+// the edge line, so Wbar_g = M Wbar and the derivative averages are M applied
+// to the components, then R to (d/dx, d/dy).
+template <typename R, int EQ>
+__device__ __forceinline__ void ghost_component(int type, const R* own, R nx, R ny, int c, const EqParams& P, R& W,
+                                                R& V, R& Y) {
+  constexpr int m = EqTraits<EQ>::m;
+  if (type == kGhostInflow) {
+    W = EqC<R>::win(P, c); V = R(0); Y = R(0);
+    return;
+  }
+  if (EQ != kEqEuler || type != kGhostWall) {
+    W = own[c]; V = own[m + c]; Y = own[2 * m + c];
+    return;
+  }
+  W = mirror_c(nx, ny, own, c);
+  const R vm = mirror_c(nx, ny, own + m, c), ym = mirror_c(nx, ny, own + 2 * m, c);
+  const R dn = vm * nx + ym * ny;
+  V = vm - R(2) * nx * dn;
+  Y = ym - R(2) * ny * dn;
+}
 
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
@@ -318,6 +363,15 @@ __device__ __forceinline__ R spectral_radius_all(const R* W, const EqParams& P) 
   }
 }
 
+// Floor of the scale limiter: min(1e-13, rho_bar, p_bar) in double (Zhang and
+// Shu's choice).  In float the floor is min(2^-20, rho_bar, p_bar): a point
+// density pulled down to 1e-13 next to an O(1) momentum overflows the float
+// Lax-Wendroff jets (their second derivatives carry 1 / rho^3).
+__device__ __forceinline__ double positivity_floor(double rho, double p) { return fmin(1e-13, fmin(rho, p)); }
+__device__ __forceinline__ float positivity_floor(float rho, float p) {
+  return fminf(9.5367431640625e-07f, fminf(rho, p));
+}
+
 // Scale limiter (Zhang and Shu), Euler.  Pressure of a conservative state.
 template <typename R> __device__ __forceinline__ R pressure_of(R gam, const R* W) {
   return (gam - R(1)) * (W[3] - R(0.5) * (W[1] * W[1] + W[2] * W[2]) / W[0]);
@@ -345,6 +399,14 @@ template <typename R> __device__ __forceinline__ R pressure_root(R gam, const R 
     tk = best < R(0) ? R(0) : (best > R(1) ? R(1) : best);
   }
   return tk;
+}
+
+// Single precision: the quadratic's coefficients cancel badly in float near
+// the admissible boundary, so the root is taken in double (a rare path: only
+// where the pressure bound is active).
+__device__ __forceinline__ float pressure_root(float gam, const float Wb[4], const float d[4], float eps) {
+  const double Wd[4] = {Wb[0], Wb[1], Wb[2], Wb[3]}, dd[4] = {d[0], d[1], d[2], d[3]};
+  return (float)pressure_root<double>((double)gam, Wd, dd, (double)eps);
 }
 
 // Largest f in [0, 1] such that Wb + f (w - Wb) has density and pressure >= eps:

@@ -24,13 +24,19 @@ enum RGeo : int {
   G_NRM = 76,  // 6: canonical unit normal of local edge j (outward of the lower-numbered cell)
   G_EL = 82,   // 3: |e_j| / |K|
   G_INR = 85,  // 1: inradius 2|K| / perimeter
-  NRGEO = 86
+  G_PK = 86,   // 1: perimeter / |K| of the cell        } positivity-preserving flux blending
+  G_PN = 87,   // 3: perimeter / |K| of the neighbour    } (scale limiter on); the ghost of a
+               //    across local edge j                 } boundary edge is the cell itself
+  NRGEO = 90
 };
+// Planes of the step without the scale limiter (and of the adjoint step).
+constexpr int kStepPlanes = G_INR + 1;
 // Per-cell integer planes.
 enum IGeo : int {
   I_NBR = 0,   // 3: neighbour across local edge j (internal numbering), -1 on a boundary
   I_NBE = 3,   // 1: packed: bits 2j, 2j+1: the neighbour's local index of edge j; bit 6 + j: this cell
-               //    owns edge j (lower index in the caller's numbering, or a boundary edge)
+               //    owns edge j (lower index in the caller's numbering, or a boundary edge); bits
+               //    9 + 2j, 10 + 2j: the ghost of a boundary edge j (0 transmissive, 1 wall, 2 inflow)
   NIGEO = 4
 };
 
@@ -45,6 +51,7 @@ struct HostMesh {
   std::vector<double> rgeo;       // [NRGEO * nt], internal order
   std::vector<int32_t> igeo;      // [NIGEO * nt]
   std::vector<double> area;       // [nt] internal order
+  bool special_bc = false;        // some boundary edge is a wall or an inflow edge
 };
 
 // Builds everything above; returns an error message or "" on success.

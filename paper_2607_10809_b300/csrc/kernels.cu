@@ -33,6 +33,7 @@
 // vector loads (mostly L2 hits thanks to the Hilbert order).
 #include <cuda.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "device.cuh"
@@ -210,17 +211,194 @@ __device__ __forceinline__ unsigned char* smem_base(unsigned char* raw) {
   return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
 }
 
+// Cells of a reconstruction block staged in shared memory (TMA boxes of a
+// contiguous 32-cell tile): geometry planes, neighbour indices, state records.
+template <typename R, int EQ> struct StagedCells {
+  static constexpr int m = EqTraits<EQ>::m;
+  const ReconStage<R, EQ>* S;
+  __device__ __forceinline__ R geo(int p, int lc) const { return S->geo[p][lc]; }
+  __device__ __forceinline__ const R* own(int lc) const { return S->u[lc]; }
+  __device__ __forceinline__ int nbr(int j, int lc) const { return S->idx[j][lc]; }
+  __device__ __forceinline__ int nbe(int lc) const { return S->idx[3][lc]; }
+  __device__ __forceinline__ SmemGeo<R> geo_of(int lc) const { return SmemGeo<R>{&S->geo[0][0], lc}; }
+};
+
+// Cells of a reconstruction block read straight from global memory: cells[lc]
+// is the internal index of the block's cell lc (entries beyond the block's
+// count hold a valid cell).  Used for the halo of a fused tile.
+template <typename R> struct GlobalGeo {
+  const R* __restrict__ rg;
+  int ld, i;
+  __device__ __forceinline__ R operator()(int p) const { return __ldg(rg + (size_t)p * ld + i); }
+};
+template <typename R, int EQ> struct GlobalCells {
+  static constexpr int m = EqTraits<EQ>::m;
+  const R* __restrict__ rg;
+  const int32_t* __restrict__ ig;
+  const R* __restrict__ U;
+  const int* cells;
+  int ld;
+  __device__ __forceinline__ R geo(int p, int lc) const { return __ldg(rg + (size_t)p * ld + cells[lc]); }
+  __device__ __forceinline__ const R* own(int lc) const { return U + (size_t)cells[lc] * 3 * m; }
+  __device__ __forceinline__ int nbr(int j, int lc) const { return __ldg(ig + (size_t)(I_NBR + j) * ld + cells[lc]); }
+  __device__ __forceinline__ int nbe(int lc) const { return __ldg(ig + (size_t)I_NBE * ld + cells[lc]); }
+  __device__ __forceinline__ GlobalGeo<R> geo_of(int lc) const { return GlobalGeo<R>{rg, ld, cells[lc]}; }
+};
+
+// Reconstruction (Steps 1-6) and the Lax-Wendroff procedure at the six edge
+// Gauss points of up to kCells cells.  NT: threads of the block; phase A runs
+// the (cell, component) tasks and phase B the (cell, point) tasks in passes of
+// NT; the limiter's phase B synchronises per point and needs one thread per
+// (cell, point).  out(lc, qp, rec) stores the Taylor record (W, W_t, W_tt) of
+// point qp of cell lc.  U: the state (neighbour records); dtr: the time step.
+template <typename R, int EQ, bool LIM, int NT, typename Src, typename Out>
+__device__ __forceinline__ void recon_lw_block(const Src& src, int count, const R* __restrict__ U, R dtr,
+                                               const EqParams& P, R (*qs)[6][kCells], R (*lim)[kCells], Out out) {
+  constexpr int m = EqTraits<EQ>::m;
+  static_assert(!LIM || NT == 6 * kCells, "the limiter path takes one thread per (cell, point)");
+  const int t = threadIdx.x;
+  for (int task = t; task < m * kCells; task += NT) {
+    const int lc = task % kCells, c = task / kCells;
+    if (lc < count) {
+      R Wl[3], Vl[3], Yl[3];
+      const R* own = src.own(lc);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int nb = src.nbr(j, lc);
+        if (nb >= 0) {
+          const R* rec = U + (size_t)nb * 3 * m;
+          Wl[j] = rec[0 * m + c]; Vl[j] = rec[1 * m + c]; Yl[j] = rec[2 * m + c];
+        } else {
+          // boundary ghost: outward unit normal of edge j from the scaled vertices
+          const int jn = (j + 1) % 3;
+          const R dx = src.geo(G_VX + 2 * jn, lc) - src.geo(G_VX + 2 * j, lc);
+          const R dy = src.geo(G_VX + 2 * jn + 1, lc) - src.geo(G_VX + 2 * j + 1, lc);
+          const R il = R(1) / sqrt(dx * dx + dy * dy);
+          ghost_component<R, EQ>(ghost_type(src.nbe(lc), j), own, dy * il, -dx * il, c, P, Wl[j], Vl[j], Yl[j]);
+        }
+      }
+      R q[6];
+      reconstruct_component<R>(src.geo_of(lc), own[0 * m + c], own[1 * m + c], own[2 * m + c], Wl, Vl, Yl, P, q);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) qs[c][k][lc] = q[k];
+    }
+  }
+  __syncthreads();
+  for (int task = t; task < 6 * kCells; task += NT) {
+    const int lc = task % kCells, qp = task / kCells;
+    const bool act = lc < count;
+    R W[m], Wx[m], Wy[m], Wxx[m], Wxy[m], Wyy[m], Wt[m], Wtt[m];
+    if (act) {
+      const int j = qp >> 1, g = qp & 1, jn = (j + 1) % 3;
+      const R sg = g == 0 ? R(0.5) - R(0.28867513459481288225) : R(0.5) + R(0.28867513459481288225);
+      const R xj = src.geo(G_VX + 2 * j, lc), yj = src.geo(G_VX + 2 * j + 1, lc);
+      const R xi = xj + sg * (src.geo(G_VX + 2 * jn, lc) - xj);
+      const R et = yj + sg * (src.geo(G_VX + 2 * jn + 1, lc) - yj);
+      const R ih = src.geo(G_IH, lc), ih2 = ih * ih;
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const R q0 = qs[c][0][lc], q1 = qs[c][1][lc], q2 = qs[c][2][lc];
+        const R q3 = qs[c][3][lc], q4 = qs[c][4][lc], q5 = qs[c][5][lc];
+        W[c] = q0 + xi * (q1 + q3 * xi + q4 * et) + et * (q2 + q5 * et);
+        Wx[c] = (q1 + R(2) * q3 * xi + q4 * et) * ih;
+        Wy[c] = (q2 + q4 * xi + R(2) * q5 * et) * ih;
+        Wxx[c] = R(2) * q3 * ih2; Wxy[c] = q4 * ih2; Wyy[c] = R(2) * q5 * ih2;
+      }
+    }
+    if constexpr (EQ == kEqEuler && LIM) {
+      // scale limiter: spatial scaling over the six Gauss points, then the
+      // Lax-Wendroff data, then scaling of the space-time Taylor data over
+      // the points and the three time nodes
+      const R gam = EqC<R>::gam(P);
+      R Wb[4] = {R(0), R(0), R(0), R(0)};
+      if (act) {
+        const R* own = src.own(lc);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Wb[c] = own[c];
+      }
+      const R pb0 = act ? pressure_of(gam, Wb) : R(0);
+      const bool ok = act && Wb[0] > R(0) && pb0 > R(0);
+      const R eps = ok ? positivity_floor(Wb[0], pb0) : R(0);
+      if (act) lim[qp][lc] = W[0];
+      __syncthreads();
+      R th1 = R(1), th2 = R(1);
+      if (ok) {
+        R rmin = lim[0][lc];
+#pragma unroll
+        for (int k = 1; k < 6; ++k) rmin = lim[k][lc] < rmin ? lim[k][lc] : rmin;
+        if (rmin < eps) th1 = (Wb[0] - eps) / (Wb[0] - rmin);
+      }
+      __syncthreads();
+      R f = R(1);
+      if (ok) {
+        R w[4] = {Wb[0] + th1 * (W[0] - Wb[0]), W[1], W[2], W[3]};
+        if (pressure_of(gam, w) < eps) {
+          R d[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) d[c] = w[c] - Wb[c];
+          f = pressure_root(gam, Wb, d, eps);
+        }
+      }
+      if (act) lim[qp][lc] = f;
+      __syncthreads();
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) th2 = lim[k][lc] < th2 ? lim[k][lc] : th2;
+      }
+      __syncthreads();
+      if (ok && (th1 != R(1) || th2 != R(1))) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const R th = c == 0 ? th1 * th2 : th2;
+          W[c] = Wb[c] + th * (W[c] - Wb[c]);
+          Wx[c] *= th; Wy[c] *= th; Wxx[c] *= th; Wxy[c] *= th; Wyy[c] *= th;
+        }
+      }
+      if (act) lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
+      R ft = R(1);
+      if (ok) {
+        const R tau[3] = {R(0), R(0.5) * dtr, dtr};
+#pragma unroll
+        for (int si = 0; si < 3; ++si) {
+          R w[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) w[c] = W[c] + Wt[c] * tau[si] + Wtt[c] * (R(0.5) * tau[si] * tau[si]);
+          const R fs = admissible_fraction(gam, Wb, w, eps);
+          ft = fs < ft ? fs : ft;
+        }
+      }
+      if (act) lim[qp][lc] = ft;
+      __syncthreads();
+      R tht = R(1);
+      if (ok) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) tht = lim[k][lc] < tht ? lim[k][lc] : tht;
+      }
+      if (ok && tht != R(1)) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { W[c] = Wb[c] + tht * (W[c] - Wb[c]); Wt[c] *= tht; Wtt[c] *= tht; }
+      }
+    } else if (act) {
+      lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
+    }
+    if (act) {
+      R rec[3 * m];
+#pragma unroll
+      for (int c = 0; c < m; ++c) { rec[c] = W[c]; rec[m + c] = Wt[c]; rec[2 * m + c] = Wtt[c]; }
+      out(lc, qp, rec);
+    }
+  }
+  __syncthreads();
+}
+
 // Reconstruction + Lax-Wendroff over the context's tiles (double-buffered TMA
-// staging).  bar: two initialised mbarriers, ph: their phase bits (kept across
-// calls).  Returns false if a bounded wait gave up (flag 2 raised).
-// NT: threads of the block.  Phase A runs the (cell, component) tasks and
-// phase B the (cell, point) tasks in passes of NT; the limiter's phase B
-// synchronises per point and needs one thread per (cell, point).
+// staging), writing the edge-point records to Pb.  bar: two initialised
+// mbarriers, ph: their phase bits (kept across calls).  Returns false if a
+// bounded wait gave up (flag 2 raised).
 template <typename R, int EQ, bool LIM, int NT, typename Ctx>
 __device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap* mIdx, const EqParams& P,
                             R* __restrict__ Pb, unsigned char* base, uint64_t* bar, unsigned* ph) {
   constexpr int m = EqTraits<EQ>::m;
-  static_assert(!LIM || NT == 6 * kCells, "the limiter path takes one thread per (cell, point)");
   using Stage = ReconStage<R, EQ>;
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*qs)[6][kCells] = reinterpret_cast<R (*)[6][kCells]>(base + 2 * sizeof(Stage));
@@ -259,129 +437,11 @@ __device__ bool recon_phase(Ctx& ctx, const CUtensorMap* mGeo, const CUtensorMap
     }
     int cell0, count;
     ctx.range(tile, cell0, count);
-    const R* U = ctx.uin(tile);
     const R dtr = R(ctx.dt_of(tile));   // time nodes of the limiter
-    const Stage& S = st[s];
-    for (int task = t; task < m * kCells; task += NT) {
-      const int lc = task % kCells, c = task / kCells;
-      if (lc < count) {
-        R Wl[3], Vl[3], Yl[3];
-        const R* own = S.u[lc];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const int nb = S.idx[j][lc];
-          const R* rec = nb >= 0 ? U + (size_t)nb * 3 * m : own;   // transmissive ghost: own data
-          Wl[j] = rec[0 * m + c]; Vl[j] = rec[1 * m + c]; Yl[j] = rec[2 * m + c];
-        }
-        R q[6];
-        reconstruct_component<R>(SmemGeo<R>{&S.geo[0][0], lc}, own[0 * m + c], own[1 * m + c], own[2 * m + c], Wl, Vl,
-                                 Yl, P, q);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) qs[c][k][lc] = q[k];
-      }
-    }
-    __syncthreads();
-    for (int task = t; task < 6 * kCells; task += NT) {
-      const int lc = task % kCells, qp = task / kCells, i = cell0 + lc;
-      const bool act = lc < count;
-      R W[m], Wx[m], Wy[m], Wxx[m], Wxy[m], Wyy[m], Wt[m], Wtt[m];
-      if (act) {
-        const int j = qp >> 1, g = qp & 1, jn = (j + 1) % 3;
-        const R sg = g == 0 ? R(0.5) - R(0.28867513459481288225) : R(0.5) + R(0.28867513459481288225);
-        const R xi = S.geo[G_VX + 2 * j][lc] + sg * (S.geo[G_VX + 2 * jn][lc] - S.geo[G_VX + 2 * j][lc]);
-        const R et = S.geo[G_VX + 2 * j + 1][lc] + sg * (S.geo[G_VX + 2 * jn + 1][lc] - S.geo[G_VX + 2 * j + 1][lc]);
-        const R ih = S.geo[G_IH][lc], ih2 = ih * ih;
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          const R q0 = qs[c][0][lc], q1 = qs[c][1][lc], q2 = qs[c][2][lc];
-          const R q3 = qs[c][3][lc], q4 = qs[c][4][lc], q5 = qs[c][5][lc];
-          W[c] = q0 + xi * (q1 + q3 * xi + q4 * et) + et * (q2 + q5 * et);
-          Wx[c] = (q1 + R(2) * q3 * xi + q4 * et) * ih;
-          Wy[c] = (q2 + q4 * xi + R(2) * q5 * et) * ih;
-          Wxx[c] = R(2) * q3 * ih2; Wxy[c] = q4 * ih2; Wyy[c] = R(2) * q5 * ih2;
-        }
-      }
-      if constexpr (EQ == kEqEuler && LIM) {
-        // scale limiter: spatial scaling over the six Gauss points, then the
-        // Lax-Wendroff data, then scaling of the space-time Taylor data over
-        // the points and the three time nodes
-        const R gam = EqC<R>::gam(P);
-        R Wb[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) Wb[c] = S.u[lc][c];
-        const R pb0 = act ? pressure_of(gam, Wb) : R(0);
-        const bool ok = act && Wb[0] > R(0) && pb0 > R(0);
-        const R eps = ok ? fmin(R(1e-13), fmin(Wb[0], pb0)) : R(0);
-        if (act) lim[qp][lc] = W[0];
-        __syncthreads();
-        R th1 = R(1), th2 = R(1);
-        if (ok) {
-          R rmin = lim[0][lc];
-#pragma unroll
-          for (int k = 1; k < 6; ++k) rmin = lim[k][lc] < rmin ? lim[k][lc] : rmin;
-          if (rmin < eps) th1 = (Wb[0] - eps) / (Wb[0] - rmin);
-        }
-        __syncthreads();
-        R f = R(1);
-        if (ok) {
-          R w[4] = {Wb[0] + th1 * (W[0] - Wb[0]), W[1], W[2], W[3]};
-          if (pressure_of(gam, w) < eps) {
-            R d[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) d[c] = w[c] - Wb[c];
-            f = pressure_root(gam, Wb, d, eps);
-          }
-        }
-        if (act) lim[qp][lc] = f;
-        __syncthreads();
-        if (ok) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) th2 = lim[k][lc] < th2 ? lim[k][lc] : th2;
-        }
-        __syncthreads();
-        if (ok && (th1 != R(1) || th2 != R(1))) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const R th = c == 0 ? th1 * th2 : th2;
-            W[c] = Wb[c] + th * (W[c] - Wb[c]);
-            Wx[c] *= th; Wy[c] *= th; Wxx[c] *= th; Wxy[c] *= th; Wyy[c] *= th;
-          }
-        }
-        if (act) lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
-        R ft = R(1);
-        if (ok) {
-          const R tau[3] = {R(0), R(0.5) * dtr, dtr};
-#pragma unroll
-          for (int si = 0; si < 3; ++si) {
-            R w[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) w[c] = W[c] + Wt[c] * tau[si] + Wtt[c] * (R(0.5) * tau[si] * tau[si]);
-            const R fs = admissible_fraction(gam, Wb, w, eps);
-            ft = fs < ft ? fs : ft;
-          }
-        }
-        if (act) lim[qp][lc] = ft;
-        __syncthreads();
-        R tht = R(1);
-        if (ok) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) tht = lim[k][lc] < tht ? lim[k][lc] : tht;
-        }
-        if (ok && tht != R(1)) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) { W[c] = Wb[c] + tht * (W[c] - Wb[c]); Wt[c] *= tht; Wtt[c] *= tht; }
-        }
-      } else if (act) {
-        lax_wendroff<R, EQ>(W, Wx, Wy, Wxx, Wxy, Wyy, P, Wt, Wtt);
-      }
-      if (act) {
-        R rec[3 * m];
-#pragma unroll
-        for (int c = 0; c < m; ++c) { rec[c] = W[c]; rec[m + c] = Wt[c]; rec[2 * m + c] = Wtt[c]; }
-        copy_rec<R, 3 * m>(Pb + (size_t)i * 18 * m + qp * 3 * m, rec);
-      }
-    }
-    __syncthreads();
+    recon_lw_block<R, EQ, LIM, NT>(StagedCells<R, EQ>{&st[s]}, count, ctx.uin(tile), dtr, P, qs, lim,
+                                   [&](int lc, int qp, const R* rec) {
+                                     copy_rec<R, 3 * m>(Pb + (size_t)(cell0 + lc) * 18 * m + qp * 3 * m, rec);
+                                   });
     tile = next;
   }
   return true;
@@ -392,6 +452,7 @@ template <typename R, int EQ> struct EdgeStage {
   static constexpr int m = EqTraits<EQ>::m;
   R geo[kEdgePlanes][kCells];    // TMA tensor box: planes x cells
   int32_t idx[4][kCells];        // TMA tensor box
+  R lg[kLimPlanes][kCells];      // TMA tensor box: flux-blending geometry (scale limiter only)
   R pb[kCells][18 * m];          // bulk copy of the tile's edge-point records
   R u[kCells][3 * m];            // bulk copy of the tile's state records
   R cc[kCells][m];               // bulk copy of the compensation words (FP32 form; else unused)
@@ -410,14 +471,268 @@ template <typename R, int EQ> constexpr size_t edge_smem_bytes() {
 // over the context's tiles.  GL = false: the three Gauss-Lobatto nodes, the
 // last of which (t_{n+1}) also gives the central values of Eq. timeflux; GL =
 // true: two Gauss-Legendre nodes and a separate Taylor evaluation at t_{n+1}.
-// Returns false if a bounded wait gave up.
+// LIM (Euler with the scale limiter): each edge flux is blended with the
+// first-order LLF flux of the two cell averages so that the new averages stay
+// admissible (see blend_theta).  Returns false if a bounded wait gave up.
 constexpr double kGaussNode = 0.28867513459481288225;   // sqrt(3) / 6
 
-template <typename R, int EQ, bool GL, typename Ctx>
-__device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap* mIdx, const EqParams& P,
-                           const R* __restrict__ Pb, unsigned char* base, uint64_t* bar, unsigned* ph) {
+// Positivity-preserving flux blending (Hu, Adams and Shu 2013), Euler, with
+// the scale limiter.  The limiter keeps the point values admissible, but a
+// one-step update built from time-Taylor values is not a convex combination of
+// them, so a new cell average can still lose positivity.  Each average is
+//   Wbar^{n+1} = sum_e (|e| / P) Phi_e,  Phi_e = Wbar - (dt P / |K|) (Fhat_e - F(Wbar) . n_e)
+// (P the perimeter; the |e| n_e of a cell sum to zero); with Fhat = FL + theta
+// (FH - FL), FL the first-order LLF flux of the two averages (same alpha),
+// theta is the largest value in [0, 1] that keeps Phi_e admissible on both
+// sides.  Inputs in the edge's canonical orientation (n outward of the left
+// cell): averages WL, WR, their F.n HL, HR, the blended fluxes' end points FL,
+// FH, and lamL = dt P_L / |K_L|, lamR likewise (lamR < 0 ignored: boundary).
+template <typename R>
+__device__ __forceinline__ R blend_theta(R gam, const R WL[4], const R WR[4], const R HL[4], const R HR[4],
+                                         const R FL[4], const R FH[4], R lamL, R lamR) {
+  R theta = R(1);
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const R* Wk = side == 0 ? WL : WR;
+    const R* Hk = side == 0 ? HL : HR;
+    const R lam = side == 0 ? lamL : -lamR;   // the normal points into the right cell
+    if (side == 1 && lamR < R(0)) break;
+    const R pk = pressure_of(gam, Wk);
+    if (!(Wk[0] > R(0)) || !(pk > R(0))) continue;   // the average itself is not admissible
+    const R eps = positivity_floor(Wk[0], pk);
+    R phi0[4], phi1[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      phi0[c] = Wk[c] - lam * (FL[c] - Hk[c]);
+      phi1[c] = Wk[c] - lam * (FH[c] - Hk[c]);
+    }
+    R th = R(0);
+    if (phi0[0] >= eps && pressure_of(gam, phi0) >= eps) th = admissible_fraction(gam, phi0, phi1, eps);
+    theta = th < theta ? th : theta;
+  }
+  return theta;
+}
+
+// Flux at the time nodes, cell-average and Green-Gauss update and CFL
+// candidates of up to kCells cells whose flux geometry, indices, state and
+// compensation words are staged in S (members geo, idx, lg, u, cc).  recs
+// gives the Taylor records: recs.mine(lc, q) of the cell's own point q,
+// recs.theirs(lc, j, nb, qn) the record of point qn of the neighbour nb
+// across edge j.  part, wn: shared scratch.
+template <typename R, int EQ, bool GL, bool LIM, typename Ctx, typename FS, typename Recs>
+__device__ __forceinline__ void flux_update_block(Ctx& ctx, int tile, int cell0, int count, const FS& S,
+                                                  const Recs& recs, const R* __restrict__ U, R* __restrict__ Un,
+                                                  R dtr, const EqParams& P, R (*part)[EqTraits<EQ>::m][6][kCells],
+                                                  R (*wn)[kCells]) {
   constexpr int m = EqTraits<EQ>::m;
+  const int t = threadIdx.x;
+  {
+    const int lc = t % kCells, qp = t / kCells;
+    const bool act = lc < count;
+    const int j = qp >> 1, gm = qp & 1;
+    R Wi[m], Wn[m], Fe[m], Sh[m];
+    R nx = R(0), ny = R(0), el = R(0), alpha = R(0);
+    bool left = true;
+    int nb = -1;
+    if (act) {
+      nb = S.idx[j][lc];
+      const int je = (S.idx[3][lc] >> (2 * j)) & 3;
+      left = (S.idx[3][lc] >> (6 + j)) & 1;   // this cell owns the edge: canonical left side
+      nx = S.geo[2 * j][lc]; ny = S.geo[2 * j + 1][lc];
+      el = S.geo[6 + j][lc];
+      copy_rec<R, m>(Wi, S.u[lc]);
+      const int gtype = nb >= 0 ? kGhostTransmissive : ghost_type(S.idx[3][lc], j);
+      if (nb >= 0) {
+        copy_rec<R, m>(Wn, U + (size_t)nb * 3 * m);
+      } else {
+        // the ghost's average; a boundary edge belongs to its cell, so n is outward
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          R v, yv;
+          ghost_component<R, EQ>(gtype, S.u[lc], nx, ny, c, P, Wn[c], v, yv);
+        }
+      }
+      R aL, aR;
+      if (left) { aL = spectral_radius_n<R, EQ>(Wi, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wn, nx, ny, P); }
+      else      { aL = spectral_radius_n<R, EQ>(Wn, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wi, nx, ny, P); }
+      alpha = aL > aR ? aL : aR;
+      // this cell's Taylor data at its point (j, gm); the neighbour's at the
+      // same physical point, its point (je, 1 - gm); canonical left / right
+      const int qm = 2 * j + gm, qn = 2 * je + (1 - gm);
+      R mine[3 * m], theirs[3 * m];
+      copy_rec<R, 3 * m>(mine, recs.mine(lc, qm));
+      if (nb >= 0) {
+        copy_rec<R, 3 * m>(theirs, recs.theirs(lc, j, nb, qn));
+      } else if (gtype == kGhostInflow) {   // the imposed state, constant in time
+#pragma unroll
+        for (int c = 0; c < m; ++c) { theirs[c] = EqC<R>::win(P, c); theirs[m + c] = R(0); theirs[2 * m + c] = R(0); }
+      } else if (EQ == kEqEuler && gtype == kGhostWall) {   // the mirrored interior Taylor data
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int c = 0; c < m; ++c) theirs[k * m + c] = mirror_c(nx, ny, mine + k * m, c);
+      } else {
+        copy_rec<R, 3 * m>(theirs, mine);   // transmissive: W^ext = W^int
+      }
+      R a0[m], a1[m], a2[m], b0[m], b1[m], b2[m];
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        a0[c] = left ? mine[c] : theirs[c];
+        a1[c] = left ? mine[m + c] : theirs[m + c];
+        a2[c] = left ? mine[2 * m + c] : theirs[2 * m + c];
+        b0[c] = left ? theirs[c] : mine[c];
+        b1[c] = left ? theirs[m + c] : mine[m + c];
+        b2[c] = left ? theirs[2 * m + c] : mine[2 * m + c];
+      }
+      constexpr int ns = GL ? 2 : 3;   // time nodes
+      R tau[3], wts[3];
+      if constexpr (GL) {
+        tau[0] = dtr * R(0.5 - kGaussNode); tau[1] = dtr * R(0.5 + kGaussNode);
+        wts[0] = R(0.5); wts[1] = R(0.5);
+      } else {
+        tau[0] = R(0); tau[1] = R(0.5) * dtr; tau[2] = dtr;
+        wts[0] = R(1.0 / 6.0); wts[1] = R(4.0 / 6.0); wts[2] = R(1.0 / 6.0);
+      }
+#pragma unroll
+      for (int c = 0; c < m; ++c) Fe[c] = R(0);
+#pragma unroll
+      for (int si = 0; si < ns; ++si) {
+        R WL[m], WR[m], HL[m], HR[m];
+        const R hs = R(0.5) * tau[si] * tau[si];
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          WL[c] = a0[c] + tau[si] * a1[c] + hs * a2[c];
+          WR[c] = b0[c] + tau[si] * b1[c] + hs * b2[c];
+        }
+        flux_n<R, EQ>(WL, nx, ny, P, HL);
+        flux_n<R, EQ>(WR, nx, ny, P, HR);
+#pragma unroll
+        for (int c = 0; c < m; ++c) Fe[c] += wts[si] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
+        if (!GL && si == 2) {
+#pragma unroll
+          for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
+        }
+      }
+      if constexpr (GL) {   // Eq. timeflux from its own Taylor evaluation at t_{n+1}
+        const R hs = R(0.5) * dtr * dtr;
+#pragma unroll
+        for (int c = 0; c < m; ++c)
+          Sh[c] = R(0.5) * ((a0[c] + dtr * a1[c] + hs * a2[c]) + (b0[c] + dtr * b1[c] + hs * b2[c]));
+      }
+    }
+    if constexpr (LIM) {
+      // flux blending: the edge's high-order flux is the mean of its two
+      // Gauss points' (the same sum on both sides of the edge)
+      if (act) {
+#pragma unroll
+        for (int c = 0; c < m; ++c) part[0][c][qp][lc] = Fe[c];
+      }
+      __syncthreads();
+      if (act) {
+        R FH[4], FL[4], WL[4], WR[4], HL[4], HR[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          FH[c] = R(0.5) * (part[0][c][2 * j][lc] + part[0][c][2 * j + 1][lc]);
+          WL[c] = left ? Wi[c] : Wn[c];
+          WR[c] = left ? Wn[c] : Wi[c];
+        }
+        flux_n<R, EQ>(WL, nx, ny, P, HL);
+        flux_n<R, EQ>(WR, nx, ny, P, HR);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) FL[c] = R(0.5) * (HL[c] + HR[c] - alpha * (WR[c] - WL[c]));
+        const R pown = S.lg[0][lc], pnb = S.lg[1 + j][lc];
+        const R lamL = dtr * (left ? pown : pnb);
+        const R lamR = nb >= 0 ? dtr * (left ? pnb : pown) : R(-1);
+        const R theta = blend_theta(EqC<R>::gam(P), WL, WR, HL, HR, FL, FH, lamL, lamR);
+        if (theta < R(1)) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) Fe[c] = FL[c] + theta * (Fe[c] - FL[c]);
+        }
+      }
+      __syncthreads();
+    }
+    if (act) {
+      // Gauss weight 1/2 and the cell's outward normal (+-n).  In FP32 the
+      // Green-Gauss terms are taken relative to the cell's own average: the
+      // cell's |e| n sum to zero, so the result is the same, while the terms
+      // shrink from |W| / h to |grad W| and their rounding with them.
+      const R sgn = left ? R(0.5) * el : R(-0.5) * el;
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        const R sh = sizeof(R) == 4 ? Sh[c] - Wi[c] : Sh[c];
+        part[0][c][qp][lc] = sgn * Fe[c];
+        part[1][c][qp][lc] = sgn * nx * sh;
+        part[2][c][qp][lc] = sgn * ny * sh;
+      }
+    }
+  }
+  __syncthreads();
+  // sums of the six shares: thread (cell, output) for the 3m outputs
+  for (int k = t; k < 3 * m * kCells; k += kThreads) {
+    const int lc = k % kCells, o = k / kCells;   // o = kind * m + c
+    if (lc < count) {
+      const int kind = o / m, c = o % m;
+      R r = R(0);
+#pragma unroll
+      for (int qp = 0; qp < 6; ++qp) r += part[kind][c][qp][lc];
+      R v = r;
+      if (kind == 0) {
+        R* Cp = ctx.comp(tile);
+        if (Cp) {
+          // compensated summation of the updates: the rounding error of each
+          // new average is carried into the next update, so that the FP32
+          // averages do not accumulate one rounding per step
+          const R y = -dtr * r - S.cc[lc][c];
+          const R w = S.u[lc][c];
+          v = w + y;
+          Cp[(size_t)(cell0 + lc) * m + c] = (v - w) - y;
+        } else {
+          v = S.u[lc][c] - dtr * r;
+        }
+        wn[c][lc] = v;
+      }
+      Un[(size_t)(cell0 + lc) * 3 * m + o] = v;
+    }
+  }
+  __syncthreads();
+  if (t < kCells) {
+    double v = dinf();
+    if (t < count) {
+      R Wnew[m];
+#pragma unroll
+      for (int c = 0; c < m; ++c) Wnew[c] = wn[c][t];
+      if (!physical<R, EQ>(Wnew, P)) ctx.bad_cell(tile);
+      const R lam = spectral_radius_all<R, EQ>(Wnew, P);
+      if (lam > R(0)) {
+        const double r = (double)(S.geo[G_INR - G_NRM][t] / lam);
+        if (r >= 0) v = r;
+      }
+    }
+    ctx.tile_min(tile, v);
+  }
+  __syncthreads();
+}
+
+// Edge-point records of a tile staged in an EdgeStage (own) and in global
+// memory (neighbours).
+template <typename R, int EQ> struct StagedRecs {
+  static constexpr int m = EqTraits<EQ>::m;
+  const EdgeStage<R, EQ>* S;
+  const R* __restrict__ Pb;
+  __device__ __forceinline__ const R* mine(int lc, int q) const { return &S->pb[lc][q * 3 * m]; }
+  __device__ __forceinline__ const R* theirs(int, int, int nb, int qn) const {
+    return Pb + (size_t)nb * 18 * m + qn * 3 * m;
+  }
+};
+
+template <typename R, int EQ, bool GL, bool LIM, typename Ctx>
+__device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap* mIdx, const CUtensorMap* mLgeo,
+                           const EqParams& P, const R* __restrict__ Pb, unsigned char* base, uint64_t* bar,
+                           unsigned* ph) {
+  constexpr int m = EqTraits<EQ>::m;
+  static_assert(!LIM || EQ == kEqEuler, "flux blending is for the Euler equations");
   using Stage = EdgeStage<R, EQ>;
+  static_assert(offsetof(Stage, lg) % 128 == 0, "TMA destination alignment");
   Stage* st = reinterpret_cast<Stage*>(base);
   R (*part)[m][6][kCells] = reinterpret_cast<R (*)[m][6][kCells]>(base + 2 * sizeof(Stage));
   R (*wn)[kCells] = reinterpret_cast<R (*)[kCells]>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells);
@@ -428,9 +743,11 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
     int c0, cnt;
     ctx.range(tile, c0, cnt);
     const R* C = ctx.comp(tile);
-    mbar_arrive_expect_tx(&bar[s], C ? kBytes : kBytes - (unsigned)sizeof(Stage::cc));
+    mbar_arrive_expect_tx(&bar[s], kBytes - (C ? 0u : (unsigned)sizeof(Stage::cc)) -
+                                       (LIM ? 0u : (unsigned)sizeof(Stage::lg)));
     tma_load_2d(&st[s].geo[0][0], mEgeo, c0, 0, &bar[s]);
     tma_load_2d(&st[s].idx[0][0], mIdx, c0, 0, &bar[s]);
+    if (LIM) tma_load_2d(&st[s].lg[0][0], mLgeo, c0, 0, &bar[s]);
     bulk_load(&st[s].pb[0][0], Pb + (size_t)c0 * 18 * m, kCells * 18 * m * sizeof(R), &bar[s]);
     bulk_load(&st[s].u[0][0], ctx.uin(tile) + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
     if (C) bulk_load(&st[s].cc[0][0], C + (size_t)c0 * m, kCells * m * sizeof(R), &bar[s]);
@@ -462,135 +779,7 @@ __device__ bool edge_phase(Ctx& ctx, const CUtensorMap* mEgeo, const CUtensorMap
     R* Un = ctx.uout(tile);
     const R dtr = R(ctx.dt_of(tile));
     const Stage& S = st[s];
-    {
-      const int lc = t % kCells, qp = t / kCells;
-      if (lc < count) {
-        const int j = qp >> 1, gm = qp & 1;
-        const int nb = S.idx[j][lc];
-        const int je = (S.idx[3][lc] >> (2 * j)) & 3;
-        const bool left = (S.idx[3][lc] >> (6 + j)) & 1;   // this cell owns the edge: canonical left side
-        const R nx = S.geo[2 * j][lc], ny = S.geo[2 * j + 1][lc];
-        const R el = S.geo[6 + j][lc];
-        R Wi[m], Wn[m];
-        copy_rec<R, m>(Wi, S.u[lc]);
-        if (nb >= 0) copy_rec<R, m>(Wn, U + (size_t)nb * 3 * m);
-        else copy_rec<R, m>(Wn, Wi);
-        R aL, aR;
-        if (left) { aL = spectral_radius_n<R, EQ>(Wi, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wn, nx, ny, P); }
-        else      { aL = spectral_radius_n<R, EQ>(Wn, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wi, nx, ny, P); }
-        const R alpha = aL > aR ? aL : aR;
-        // this cell's Taylor data at its point (j, gm); the neighbour's at the
-        // same physical point, its point (je, 1 - gm); canonical left / right
-        const int qm = 2 * j + gm, qn = 2 * je + (1 - gm);
-        R mine[3 * m], theirs[3 * m];
-        copy_rec<R, 3 * m>(mine, &S.pb[lc][qm * 3 * m]);
-        if (nb >= 0) copy_rec<R, 3 * m>(theirs, Pb + (size_t)nb * 18 * m + qn * 3 * m);
-        else copy_rec<R, 3 * m>(theirs, mine);   // boundary: W^ext = W^int
-        R a0[m], a1[m], a2[m], b0[m], b1[m], b2[m];
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          a0[c] = left ? mine[c] : theirs[c];
-          a1[c] = left ? mine[m + c] : theirs[m + c];
-          a2[c] = left ? mine[2 * m + c] : theirs[2 * m + c];
-          b0[c] = left ? theirs[c] : mine[c];
-          b1[c] = left ? theirs[m + c] : mine[m + c];
-          b2[c] = left ? theirs[2 * m + c] : mine[2 * m + c];
-        }
-        constexpr int ns = GL ? 2 : 3;   // time nodes
-        R tau[3], wts[3];
-        if constexpr (GL) {
-          tau[0] = dtr * R(0.5 - kGaussNode); tau[1] = dtr * R(0.5 + kGaussNode);
-          wts[0] = R(0.5); wts[1] = R(0.5);
-        } else {
-          tau[0] = R(0); tau[1] = R(0.5) * dtr; tau[2] = dtr;
-          wts[0] = R(1.0 / 6.0); wts[1] = R(4.0 / 6.0); wts[2] = R(1.0 / 6.0);
-        }
-        R Fe[m], Sh[m];
-#pragma unroll
-        for (int c = 0; c < m; ++c) Fe[c] = R(0);
-#pragma unroll
-        for (int si = 0; si < ns; ++si) {
-          R WL[m], WR[m], HL[m], HR[m];
-          const R hs = R(0.5) * tau[si] * tau[si];
-#pragma unroll
-          for (int c = 0; c < m; ++c) {
-            WL[c] = a0[c] + tau[si] * a1[c] + hs * a2[c];
-            WR[c] = b0[c] + tau[si] * b1[c] + hs * b2[c];
-          }
-          flux_n<R, EQ>(WL, nx, ny, P, HL);
-          flux_n<R, EQ>(WR, nx, ny, P, HR);
-#pragma unroll
-          for (int c = 0; c < m; ++c) Fe[c] += wts[si] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
-          if (!GL && si == 2) {
-#pragma unroll
-            for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
-          }
-        }
-        if constexpr (GL) {   // Eq. timeflux from its own Taylor evaluation at t_{n+1}
-          const R hs = R(0.5) * dtr * dtr;
-#pragma unroll
-          for (int c = 0; c < m; ++c)
-            Sh[c] = R(0.5) * ((a0[c] + dtr * a1[c] + hs * a2[c]) + (b0[c] + dtr * b1[c] + hs * b2[c]));
-        }
-        // Gauss weight 1/2 and the cell's outward normal (+-n).  In FP32 the
-        // Green-Gauss terms are taken relative to the cell's own average: the
-        // cell's |e| n sum to zero, so the result is the same, while the terms
-        // shrink from |W| / h to |grad W| and their rounding with them.
-        const R sgn = left ? R(0.5) * el : R(-0.5) * el;
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          const R sh = sizeof(R) == 4 ? Sh[c] - Wi[c] : Sh[c];
-          part[0][c][qp][lc] = sgn * Fe[c];
-          part[1][c][qp][lc] = sgn * nx * sh;
-          part[2][c][qp][lc] = sgn * ny * sh;
-        }
-      }
-    }
-    __syncthreads();
-    // sums of the six shares: thread (cell, output) for the 3m outputs
-    for (int k = t; k < 3 * m * kCells; k += kThreads) {
-      const int lc = k % kCells, o = k / kCells;   // o = kind * m + c
-      if (lc < count) {
-        const int kind = o / m, c = o % m;
-        R r = R(0);
-#pragma unroll
-        for (int qp = 0; qp < 6; ++qp) r += part[kind][c][qp][lc];
-        R v = r;
-        if (kind == 0) {
-          R* Cp = ctx.comp(tile);
-          if (Cp) {
-            // compensated summation of the updates: the rounding error of each
-            // new average is carried into the next update, so that the FP32
-            // averages do not accumulate one rounding per step
-            const R y = -dtr * r - S.cc[lc][c];
-            const R w = S.u[lc][c];
-            v = w + y;
-            Cp[(size_t)(cell0 + lc) * m + c] = (v - w) - y;
-          } else {
-            v = S.u[lc][c] - dtr * r;
-          }
-          wn[c][lc] = v;
-        }
-        Un[(size_t)(cell0 + lc) * 3 * m + o] = v;
-      }
-    }
-    __syncthreads();
-    if (t < kCells) {
-      double v = dinf();
-      if (t < count) {
-        R Wnew[m];
-#pragma unroll
-        for (int c = 0; c < m; ++c) Wnew[c] = wn[c][t];
-        if (!physical<R, EQ>(Wnew, P)) ctx.bad_cell(tile);
-        const R lam = spectral_radius_all<R, EQ>(Wnew, P);
-        if (lam > R(0)) {
-          const double r = (double)(S.geo[G_INR - G_NRM][t] / lam);
-          if (r >= 0) v = r;
-        }
-      }
-      ctx.tile_min(tile, v);
-    }
-    __syncthreads();
+    flux_update_block<R, EQ, GL, LIM>(ctx, tile, cell0, count, S, StagedRecs<R, EQ>{&S, Pb}, U, Un, dtr, P, part, wn);
     tile = next;
   }
   return true;
@@ -619,9 +808,19 @@ __global__ void __launch_bounds__(LIM ? kThreads : kLeanThreads) k_recon(const _
   recon_phase<R, EQ, LIM, LIM ? kThreads : kLeanThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
 }
 
-template <typename R, int EQ, bool GL>
-__global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUtensorMap mEgeo,
-                                                    const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
+// Resident blocks per SM the flux kernel is compiled for (register budget):
+// FP32 Euler takes HW_EDGE_MIN_BLOCKS (measured best), the rest the default.
+#ifndef HW_EDGE_MIN_BLOCKS
+#define HW_EDGE_MIN_BLOCKS 1
+#endif
+template <typename R, int EQ> constexpr int edge_min_blocks() {
+  return (sizeof(R) == 4 && EQ == kEqEuler) ? HW_EDGE_MIN_BLOCKS : 1;
+}
+
+template <typename R, int EQ, bool GL, bool LIM>
+__global__ void __launch_bounds__(kThreads, edge_min_blocks<R, EQ>()) k_edge(const __grid_constant__ CUtensorMap mEgeo,
+                                                    const __grid_constant__ CUtensorMap mIdx,
+                                                    const __grid_constant__ CUtensorMap mLgeo, GeoView<R> G,
                                                     const R* __restrict__ U, R* __restrict__ Un,
                                                     const R* __restrict__ Pb, R* C, EqParams P, DevScalars* sc,
                                                     double dt_fixed, TileSet ts) {
@@ -644,13 +843,208 @@ __global__ void __launch_bounds__(kThreads) k_edge(const __grid_constant__ CUten
   SingleCtx<R> ctx{ts, N, U, Un, dt, sc, dinf(), C};
   if (t == 0) {
     prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    if (LIM) prefetch_tensormap(&mLgeo);
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   __syncthreads();
   unsigned ph[2] = {0u, 0u};
-  if (!edge_phase<R, EQ, GL>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph)) ctx.local_min = dinf();
+  if (!edge_phase<R, EQ, GL, LIM>(ctx, &mEgeo, &mIdx, &mLgeo, P, Pb, base, bar, ph)) ctx.local_min = dinf();
+  finish_step(sc, ctx.local_min, dt, true);
+}
+
+// ---------------------------------------------------------------- fused step
+// One kernel for the whole step: a block takes a tile of TT consecutive
+// (Hilbert-ordered) cells, reconstructs them and runs the Lax-Wendroff
+// procedure at their edge Gauss points (32-cell sub-tiles, TMA-staged
+// geometry), does the same for the tile's halo (the cells outside the tile
+// that share an edge with it; their geometry and stencils are gathered from
+// global memory), keeps all those Taylor records in shared memory, and then
+// forms the fluxes and updates the tile's cells (32-cell sub-tiles again).  The
+// edge-point records never reach global memory; the price is the halo's
+// reconstruction, done by both tiles it borders.
+
+// Flux stage of the fused kernel: an EdgeStage without the edge-point records
+// but with the packed neighbour slots of the 32 cells.
+template <typename R, int EQ> struct FluxStage {
+  static constexpr int m = EqTraits<EQ>::m;
+  R geo[kEdgePlanes][kCells];    // TMA tensor box
+  int32_t idx[4][kCells];        // TMA tensor box
+  R lg[kLimPlanes][kCells];      // TMA tensor box (scale limiter only)
+  R u[kCells][3 * m];            // bulk copy of the state records
+  R cc[kCells][m];               // bulk copy of the compensation words (FP32 form)
+  int32_t slot[kCells];          // bulk copy of the neighbour slots
+};
+
+template <typename R, int EQ> constexpr size_t round128(size_t x) { return (x + 127) / 128 * 128; }
+
+// Shared-memory layout of the fused kernel (byte offsets from the 128-byte
+// aligned base).
+template <typename R, int EQ, int TT, int HC> struct FusedSmem {
+  static constexpr int m = EqTraits<EQ>::m;
+  static constexpr size_t stage = round128<R, EQ>(sizeof(ReconStage<R, EQ>) > sizeof(FluxStage<R, EQ>)
+                                                       ? sizeof(ReconStage<R, EQ>) : sizeof(FluxStage<R, EQ>));
+  static constexpr size_t pt = 2 * stage;                                   // [TT][18m] tile records
+  static constexpr size_t ph = pt + sizeof(R) * TT * 18 * m;                // [HC][18m] halo records
+  static constexpr size_t qs = ph + sizeof(R) * HC * 18 * m;                // [m][6][32]
+  static constexpr size_t lim = qs + sizeof(R) * m * 6 * kCells;            // [6][32]
+  static constexpr size_t part = lim + sizeof(R) * 6 * kCells;              // [3][m][6][32]
+  static constexpr size_t wn = part + sizeof(R) * 3 * m * 6 * kCells;       // [m][32]
+  static constexpr size_t hc = wn + sizeof(R) * m * kCells;                 // [HC + 32] halo cells
+  static constexpr size_t bar = round128<R, EQ>(hc + sizeof(int) * (HC + kCells));
+  static constexpr size_t bytes = bar + 2 * sizeof(uint64_t) + 128;         // + alignment slack
+};
+
+// Edge-point records of a fused tile: the tile's own in Pt (tile-local index),
+// the halo's in Ph; slot: the packed neighbour slots of the 32 cells of the
+// current sub-tile (3 x 10 bits: < TT tile-local, TT + h halo h).
+template <typename R, int EQ> struct FusedRecs {
+  static constexpr int m = EqTraits<EQ>::m;
+  const R* Pt;
+  const R* Ph;
+  const int32_t* slot;
+  int sub0;    // tile-local index of the sub-tile's first cell
+  int tt;      // cells per tile
+  int lim;     // tt + halo capacity: slots at or above it are invalid
+  __device__ __forceinline__ const R* mine(int lc, int q) const { return Pt + (size_t)(sub0 + lc) * 18 * m + q * 3 * m; }
+  __device__ __forceinline__ const R* theirs(int lc, int j, int, int qn) const {
+    int v = (slot[lc] >> (kSlotBits * j)) & kSlotNone;
+    if (v >= lim) v = sub0 + lc;   // never for tables built by the host; keeps the read in bounds
+    return (v < tt ? Pt + (size_t)v * 18 * m : Ph + (size_t)(v - tt) * 18 * m) + qn * 3 * m;
+  }
+};
+
+template <typename R, int EQ, bool GL, bool LIM, int TT, int HC>
+__global__ void __launch_bounds__(kThreads) k_fused(const __grid_constant__ CUtensorMap mGeo,
+                                                     const __grid_constant__ CUtensorMap mEgeo,
+                                                     const __grid_constant__ CUtensorMap mIdx,
+                                                     const __grid_constant__ CUtensorMap mLgeo, GeoView<R> G,
+                                                     const R* __restrict__ U, R* __restrict__ Un, R* C, EqParams P,
+                                                     DevScalars* sc, double dt_fixed, FusedTiles ft) {
+  constexpr int m = EqTraits<EQ>::m;
+  static_assert(TT % kCells == 0 && TT + HC <= kSlotNone, "tile and halo fit the slot encoding");
+  using L = FusedSmem<R, EQ, TT, HC>;
+  using RS = ReconStage<R, EQ>;
+  using FS = FluxStage<R, EQ>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  R* Pt = reinterpret_cast<R*>(base + L::pt);
+  R* Ph = reinterpret_cast<R*>(base + L::ph);
+  R (*qs)[6][kCells] = reinterpret_cast<R (*)[6][kCells]>(base + L::qs);
+  R (*lim)[kCells] = reinterpret_cast<R (*)[kCells]>(base + L::lim);
+  R (*part)[m][6][kCells] = reinterpret_cast<R (*)[m][6][kCells]>(base + L::part);
+  R (*wn)[kCells] = reinterpret_cast<R (*)[kCells]>(base + L::wn);
+  int* hcells = reinterpret_cast<int*>(base + L::hc);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + L::bar);
+  const int N = G.N, t = threadIdx.x;
+  const volatile DevScalars* vs = sc;
+  if (vs->done) {  // target reached: keep the state, preserving the buffer alternation
+    for (int tile = blockIdx.x; tile < ft.ntiles; tile += gridDim.x) {
+      const int cell0 = tile * TT, count = min(TT, N - cell0);
+      for (int k = t; k < 3 * m * count; k += kThreads) Un[(size_t)cell0 * 3 * m + k] = U[(size_t)cell0 * 3 * m + k];
+    }
+    return;
+  }
+  const double dt = dt_fixed > 0 ? dt_fixed : vs->dt;
+  const R dtr = R(dt);
+  SingleCtx<R> ctx{TileSet{nullptr, 0}, N, U, Un, dt, sc, dinf(), C};
+  if (t == 0) {
+    prefetch_tensormap(&mGeo); prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    if (LIM) prefetch_tensormap(&mLgeo);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto stage_ptr = [&](int s) { return base + (size_t)s * L::stage; };
+  auto nsub = [&](int tile) { return (min(TT, N - tile * TT) + kCells - 1) / kCells; };
+  // work items of this block, in order: per tile the reconstruction sub-tiles
+  // (kind 0), then the flux sub-tiles (kind 1)
+  struct Item { int tile, kind, sub; };
+  auto advance = [&](Item it) {
+    if (++it.sub == nsub(it.tile)) {
+      it.sub = 0;
+      if (it.kind == 0) it.kind = 1;
+      else { it.kind = 0; it.tile += gridDim.x; }
+    }
+    return it;
+  };
+  auto issue = [&](int s, const Item& it) {
+    const int c0 = it.tile * TT + it.sub * kCells;
+    if (it.kind == 0) {
+      RS* S = reinterpret_cast<RS*>(stage_ptr(s));
+      mbar_arrive_expect_tx(&bar[s], (unsigned)sizeof(RS));
+      tma_load_2d(&S->geo[0][0], &mGeo, c0, 0, &bar[s]);
+      tma_load_2d(&S->idx[0][0], &mIdx, c0, 0, &bar[s]);
+      bulk_load(&S->u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+    } else {
+      FS* S = reinterpret_cast<FS*>(stage_ptr(s));
+      const unsigned bytes = (unsigned)(sizeof(S->geo) + sizeof(S->idx) + (LIM ? sizeof(S->lg) : 0) + sizeof(S->u) +
+                                        (C ? sizeof(S->cc) : 0) + sizeof(S->slot));
+      mbar_arrive_expect_tx(&bar[s], bytes);
+      tma_load_2d(&S->geo[0][0], &mEgeo, c0, 0, &bar[s]);
+      tma_load_2d(&S->idx[0][0], &mIdx, c0, 0, &bar[s]);
+      if (LIM) tma_load_2d(&S->lg[0][0], &mLgeo, c0, 0, &bar[s]);
+      bulk_load(&S->u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[s]);
+      if (C) bulk_load(&S->cc[0][0], C + (size_t)c0 * m, kCells * m * sizeof(R), &bar[s]);
+      bulk_load(&S->slot[0], ft.slot + c0, kCells * sizeof(int32_t), &bar[s]);
+    }
+  };
+  unsigned ph[2] = {0u, 0u};
+  Item cur{(int)blockIdx.x, 0, 0};
+  if (t == 0 && cur.tile < ft.ntiles) {
+    fence_proxy_async();
+    issue(0, cur);
+  }
+  int s = 0;
+  while (cur.tile < ft.ntiles) {
+    const Item nxt = advance(cur);
+    if (t == 0 && nxt.tile < ft.ntiles) {
+      fence_proxy_async();
+      issue(s ^ 1, nxt);
+    }
+    const bool ok = mbar_wait(&bar[s], ph[s]);
+    ph[s] ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        ctx.flag(2u);
+        if (nxt.tile < ft.ntiles && mbar_wait(&bar[s ^ 1], ph[s ^ 1])) ph[s ^ 1] ^= 1u;   // drain the copy in flight
+      }
+      ctx.local_min = dinf();
+      break;
+    }
+    const int c0 = cur.tile * TT + cur.sub * kCells, count = min(kCells, N - c0);
+    if (cur.kind == 0) {
+      const RS* S = reinterpret_cast<const RS*>(stage_ptr(s));
+      R* dst = Pt + (size_t)cur.sub * kCells * 18 * m;
+      recon_lw_block<R, EQ, LIM, kThreads>(StagedCells<R, EQ>{S}, count, U, dtr, P, qs, lim,
+                                           [&](int lc, int qp, const R* rec) {
+                                             copy_rec<R, 3 * m>(dst + (size_t)lc * 18 * m + qp * 3 * m, rec);
+                                           });
+      if (cur.sub == nsub(cur.tile) - 1) {
+        // the tile's halo, 32 cells at a time (the first flux stage is in flight)
+        const int h0 = ft.halo_off[cur.tile];
+        const int H = min(ft.halo_off[cur.tile + 1] - h0, HC);
+        for (int k = t; k < HC + kCells; k += kThreads) hcells[k] = H > 0 ? ft.halo[h0 + min(k, H - 1)] : 0;
+        __syncthreads();
+        for (int hb = 0; hb < H; hb += kCells) {
+          R* hdst = Ph + (size_t)hb * 18 * m;
+          recon_lw_block<R, EQ, LIM, kThreads>(GlobalCells<R, EQ>{G.rg, G.ig, U, hcells + hb, G.ld}, min(kCells, H - hb),
+                                               U, dtr, P, qs, lim, [&](int lc, int qp, const R* rec) {
+                                                 copy_rec<R, 3 * m>(hdst + (size_t)lc * 18 * m + qp * 3 * m, rec);
+                                               });
+        }
+      }
+    } else {
+      const FS* S = reinterpret_cast<const FS*>(stage_ptr(s));
+      flux_update_block<R, EQ, GL, LIM>(ctx, 0, c0, count, *S,
+                                        FusedRecs<R, EQ>{Pt, Ph, S->slot, cur.sub * kCells, TT, TT + HC}, U, Un,
+                                        dtr, P, part, wn);
+    }
+    s ^= 1;
+    cur = nxt;
+  }
   finish_step(sc, ctx.local_min, dt, true);
 }
 
@@ -700,7 +1094,8 @@ __device__ bool grid_barrier(BatchCtl* ctl, unsigned long long spin_limit, bool 
 template <typename R, int EQ, bool LIM>
 __global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUtensorMap mGeo,
                                                      const __grid_constant__ CUtensorMap mEgeo,
-                                                     const __grid_constant__ CUtensorMap mIdx, R* U0, R* U1,
+                                                     const __grid_constant__ CUtensorMap mIdx,
+                                                     const __grid_constant__ CUtensorMap mLgeo, R* U0, R* U1,
                                                      R* __restrict__ Pb, EqParams P, BatchCtx<R> ctx, int nsolves,
                                                      double cfl, int max_steps, unsigned long long spin_limit,
                                                      int withhold_block) {
@@ -712,6 +1107,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUte
   BatchCtl* ctl = ctx.ctl;
   if (threadIdx.x == 0) {
     prefetch_tensormap(&mGeo); prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    if (LIM) prefetch_tensormap(&mLgeo);
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
@@ -726,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUte
     ok = recon_phase<R, EQ, LIM, kThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
     if (!grid_barrier(ctl, spin_limit, skip || !ok)) ok = false;
     if (!ok) break;
-    ok = edge_phase<R, EQ, false>(ctx, &mEgeo, &mIdx, P, Pb, base, bar, ph);
+    ok = edge_phase<R, EQ, false, LIM>(ctx, &mEgeo, &mIdx, &mLgeo, P, Pb, base, bar, ph);
     if (!grid_barrier(ctl, spin_limit, !ok)) ok = false;
     if (!ok) break;
     // per-solve step, status and next time step (one thread per solve)
@@ -924,15 +1320,16 @@ template <typename R, int EQ, bool LIM> int recon_cap() {
   static const int cap = resident_blocks(k_recon<R, EQ, LIM>, LIM ? kThreads : kLeanThreads, recon_smem_bytes<R, EQ>());
   return cap;
 }
-template <typename R, int EQ, bool GL> int edge_cap() {
-  static const int cap = resident_blocks(k_edge<R, EQ, GL>, kThreads, edge_smem_bytes<R, EQ>());
+template <typename R, int EQ, bool GL, bool LIM> int edge_cap() {
+  static const int cap = resident_blocks(k_edge<R, EQ, GL, LIM>, kThreads, edge_smem_bytes<R, EQ>());
   return cap;
 }
 template <typename R, int EQ> void prepare_t() {
   (void)recon_cap<R, EQ, false>();
   if constexpr (EQ == kEqEuler) (void)recon_cap<R, EQ, true>();
-  (void)edge_cap<R, EQ, false>();
-  (void)edge_cap<R, EQ, true>();
+  (void)edge_cap<R, EQ, false, false>();
+  (void)edge_cap<R, EQ, true, false>();
+  if constexpr (EQ == kEqEuler) (void)edge_cap<R, EQ, false, true>();
 }
 
 template <typename R, int EQ, bool LIM> void launch_recon_lim(const StepArgs& a, cudaStream_t st) {
@@ -953,18 +1350,57 @@ template <typename R, int EQ> void launch_recon_t(const StepArgs& a, cudaStream_
   }
   launch_recon_lim<R, EQ, false>(a, st);
 }
-template <typename R, int EQ, bool GL> void launch_edge_rule(const StepArgs& a, cudaStream_t st) {
+template <typename R, int EQ, bool GL, bool LIM> void launch_edge_rule(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
   constexpr size_t smem = edge_smem_bytes<R, EQ>();
-  const int cap = edge_cap<R, EQ, GL>();
+  const int cap = edge_cap<R, EQ, GL, LIM>();
   const int nt = a.tiles.ntiles;
-  k_edge<R, EQ, GL><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
-      a.maps->egeo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
+  k_edge<R, EQ, GL, LIM><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, smem, st>>>(
+      a.maps->egeo, a.maps->idx, a.maps->lgeo, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
       reinterpret_cast<const R*>(a.Pb), reinterpret_cast<R*>(a.C), a.P, a.sc, a.dt_fixed, a.tiles);
 }
 template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
-  if (a.P.time_rule == 1) launch_edge_rule<R, EQ, true>(a, st);
-  else launch_edge_rule<R, EQ, false>(a, st);
+  if constexpr (EQ == kEqEuler) {
+    if (a.P.positivity) {   // the Gauss-Legendre rule is refused with the limiter
+      launch_edge_rule<R, EQ, false, true>(a, st);
+      return;
+    }
+  }
+  if (a.P.time_rule == 1) launch_edge_rule<R, EQ, true, false>(a, st);
+  else launch_edge_rule<R, EQ, false, false>(a, st);
+}
+template <typename R> struct FusedShape {
+  static constexpr int TT = sizeof(R) == 4 ? kFusedTile32 : kFusedTile64;
+  static constexpr int HC = sizeof(R) == 4 ? kFusedHalo32 : kFusedHalo64;
+};
+template <typename R, int EQ, bool GL, bool LIM> int fused_cap() {
+  constexpr int TT = FusedShape<R>::TT, HC = FusedShape<R>::HC;
+  static const int cap = resident_blocks(k_fused<R, EQ, GL, LIM, TT, HC>, kThreads, FusedSmem<R, EQ, TT, HC>::bytes);
+  return cap;
+}
+template <typename R, int EQ> void prepare_fused_t() {
+  (void)fused_cap<R, EQ, false, false>();
+  (void)fused_cap<R, EQ, true, false>();
+  if constexpr (EQ == kEqEuler) (void)fused_cap<R, EQ, false, true>();
+}
+template <typename R, int EQ, bool GL, bool LIM> void launch_fused_v(const StepArgs& a, cudaStream_t st) {
+  constexpr int TT = FusedShape<R>::TT, HC = FusedShape<R>::HC;
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
+  const int cap = fused_cap<R, EQ, GL, LIM>();
+  const int nt = a.fused.ntiles;
+  k_fused<R, EQ, GL, LIM, TT, HC><<<nt < cap ? (nt > 0 ? nt : 1) : cap, kThreads, FusedSmem<R, EQ, TT, HC>::bytes, st>>>(
+      a.maps->geo, a.maps->egeo, a.maps->idx, a.maps->lgeo, G, reinterpret_cast<const R*>(a.U),
+      reinterpret_cast<R*>(a.Un), reinterpret_cast<R*>(a.C), a.P, a.sc, a.dt_fixed, a.fused);
+}
+template <typename R, int EQ> void launch_fused_t(const StepArgs& a, cudaStream_t st) {
+  if constexpr (EQ == kEqEuler) {
+    if (a.P.positivity) {   // the Gauss-Legendre rule is refused with the limiter
+      launch_fused_v<R, EQ, false, true>(a, st);
+      return;
+    }
+  }
+  if (a.P.time_rule == 1) launch_fused_v<R, EQ, true, false>(a, st);
+  else launch_fused_v<R, EQ, false, false>(a, st);
 }
 template <typename R, int EQ> void launch_cfl_t(const StepArgs& a, cudaStream_t st) {
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
@@ -993,6 +1429,8 @@ void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st) {
   launch_edge(prec, eq, a, st);
 }
 void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_cfl_t, prec, eq, a, st); }
+void launch_fused(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_fused_t, prec, eq, a, st); }
+void prepare_fused_kernel(int prec, int eq) { HW_DISPATCH(prepare_fused_t, prec, eq); }
 
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st) { k_reset<<<1, 32, 0, st>>>(sc, t, cfl); }
 
@@ -1045,7 +1483,7 @@ template <typename R, int EQ, bool LIM> cudaError_t launch_batch_t(const BatchAr
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batch<R, EQ, LIM>, a.maps->geo, a.maps->egeo, a.maps->idx,
+  return cudaLaunchKernelEx(&cfg, k_batch<R, EQ, LIM>, a.maps->geo, a.maps->egeo, a.maps->idx, a.maps->lgeo,
                             reinterpret_cast<R*>(a.U0), reinterpret_cast<R*>(a.U1), reinterpret_cast<R*>(a.Pb), a.P,
                             ctx, a.nsolves, a.cfl, a.max_steps, a.spin_limit, a.withhold_block);
 }

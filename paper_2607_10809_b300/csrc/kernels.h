@@ -17,7 +17,8 @@ constexpr int kLeanThreads = 2 * kCells;           // single-solve reconstructio
                                                    // that the (cell, component) and (cell, point) task sets
                                                    // of a tile fill whole passes (2 and 3 for the Euler system)
 constexpr int kReconPlanes = G_IH + 1;             // geometry planes 0 .. G_IH feed the reconstruction
-constexpr int kEdgePlanes = NRGEO - G_NRM;         // planes G_NRM .. G_INR feed the flux kernel
+constexpr int kEdgePlanes = G_INR + 1 - G_NRM;     // planes G_NRM .. G_INR feed the flux kernel
+constexpr int kLimPlanes = NRGEO - G_PK;           // planes G_PK .. G_PN+2: flux blending (scale limiter)
 
 inline int64_t padded_cells(int64_t n) { return (n + kCells - 1) / kCells * kCells; }
 
@@ -29,11 +30,27 @@ struct TileSet {
   int ntiles;
 };
 
+// Fused step: tiles of kFusedTile32 (FP32) or kFusedTile64 (FP64) cells, each
+// with at most as many halo cells as its halo capacity; per cell the packed
+// slots of its three neighbours in the tile's shared-memory records
+// (kSlotBits bits each: below the tile size a tile cell, above it a halo cell,
+// kSlotNone on a boundary).
+constexpr int kFusedTile32 = 128, kFusedHalo32 = 64;
+constexpr int kFusedTile64 = 64, kFusedHalo64 = 48;
+constexpr int kSlotBits = 10, kSlotNone = (1 << kSlotBits) - 1;
+struct FusedTiles {
+  const int32_t* slot;       // [ld] packed neighbour slots
+  const int32_t* halo_off;   // [ntiles + 1] offsets into halo
+  const int32_t* halo;       // halo cells of each tile, ascending internal index
+  int ntiles;
+};
+
 // TMA descriptors of one solver's geometry planes (2-D: cells x planes).
 struct TensorMaps {
   CUtensorMap geo;      // reconstruction geometry, box kCells x kReconPlanes
   CUtensorMap egeo;     // flux geometry, box kCells x kEdgePlanes
   CUtensorMap idx;      // neighbour planes + packed edge indices, box kCells x 4
+  CUtensorMap lgeo;     // flux-blending geometry (scale limiter), box kCells x kLimPlanes
 };
 
 // Per-solve device state of a batch.
@@ -72,6 +89,7 @@ struct StepArgs {
   DevScalars* sc;
   double dt_fixed;         // > 0: use this step instead of the device CFL step
   EqParams P;
+  FusedTiles fused;        // tables of the fused step (ntiles = 0: not available)
 };
 
 // Arguments of the batched persistent kernel.
@@ -127,6 +145,9 @@ void prepare_step_kernels(int prec, int eq);
 void launch_recon(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_edge(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st);
+// The fused reconstruct-and-flux kernel (a.fused must be set).
+void launch_fused(int prec, int eq, const StepArgs& a, cudaStream_t st);
+void prepare_fused_kernel(int prec, int eq);
 void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st);
 void launch_set_target(DevScalars* sc, double T, int has_T, cudaStream_t st);

@@ -299,6 +299,26 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
     }
   }
 
+  // ---- perimeter / area of each cell and of its neighbours (one FP64 value per
+  // cell, so that both cells of an edge see the same numbers)
+  {
+    std::vector<double> pk(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+      double per = 0;
+      for (int j = 0; j < 3; ++j)
+        per += std::hypot(VX[3 * t + (j + 1) % 3] - VX[3 * t + j], VY[3 * t + (j + 1) % 3] - VY[3 * t + j]);
+      pk[t] = per / A[t];
+    }
+    for (int64_t k = 0; k < nt; ++k) {
+      const int64_t t = M.perm[k];
+      R(G_PK, k) = pk[t];
+      for (int j = 0; j < 3; ++j) {
+        const int32_t u = M.nbr_orig[3 * t + j];
+        R(G_PN + j, k) = u >= 0 ? pk[u] : pk[t];
+      }
+    }
+  }
+
   // ---- edge geometry: canonical normal, outward of the edge's owner, the
   // cell with the lower index in the caller's numbering, and computed in the
   // owner's frame: every edge gets one normal and one length whatever the

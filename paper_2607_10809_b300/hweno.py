@@ -22,10 +22,10 @@ EQUATIONS = {"advection": 0, "burgers": 1, "euler": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 
 # every symbol declared in include/hweno.h
-EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_destroy", "hw_mesh_ntri", "hw_mesh_neighbors",
+EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_set_boundary", "hw_mesh_destroy", "hw_mesh_ntri", "hw_mesh_neighbors",
             "hw_mesh_permutation", "hw_workspace_bytes", "hw_state_init", "hw_set_state", "hw_step", "hw_run_to",
             "hw_get_state", "hw_conservation", "hw_status_flags", "hw_time", "hw_profile", "hw_profile_read",
-            "hw_solver_destroy", "hw_last_error", "hw_step_static_scratch", "hw_batch_schedule_default",
+            "hw_solver_destroy", "hw_step_kernels", "hw_last_error", "hw_step_static_scratch", "hw_batch_schedule_default",
             "hw_batch_workspace_bytes", "hw_batch_create", "hw_batch_set_schedule", "hw_batch_get_schedule",
             "hw_batch_autotune", "hw_batch_run_to", "hw_batch_steps", "hw_batch_reset", "hw_batch_get_state",
             "hw_batch_destroy", "hw_state_bytes", "hw_state_export", "hw_state_import", "hw_host_to_internal",
@@ -40,9 +40,9 @@ class HwError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("eq", ctypes.c_int32), ("positivity", ctypes.c_int32), ("time_rule", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("ax", ctypes.c_double),
+                ("step_kernels", ctypes.c_int32), ("ax", ctypes.c_double),
                 ("ay", ctypes.c_double), ("gamma_gas", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("gamma_lin", ctypes.c_double * 4), ("eps", ctypes.c_double)]
+                ("gamma_lin", ctypes.c_double * 4), ("eps", ctypes.c_double), ("inflow", ctypes.c_double * 4)]
 
 
 class Schedule(ctypes.Structure):
@@ -71,6 +71,7 @@ def load():
         "hw_options_default": (None, [P(Options)]),
         "hw_mesh_create": (ctypes.c_int, [vp, i64, vp, i64, d, d, i32, P(vp)]),
         "hw_mesh_destroy": (ctypes.c_int, [vp]),
+        "hw_mesh_set_boundary": (ctypes.c_int, [vp, vp]),
         "hw_mesh_ntri": (i64, [vp]),
         "hw_mesh_neighbors": (ctypes.c_int, [vp, vp, vp]),
         "hw_mesh_permutation": (ctypes.c_int, [vp, vp]),
@@ -86,6 +87,7 @@ def load():
         "hw_profile": (ctypes.c_int, [vp, i32]),
         "hw_profile_read": (ctypes.c_int, [vp, vp, P(i64)]),
         "hw_solver_destroy": (ctypes.c_int, [vp]),
+        "hw_step_kernels": (ctypes.c_int, [vp, P(i32)]),
         "hw_last_error": (ctypes.c_char_p, []),
         "hw_step_static_scratch": (ctypes.c_int, [vp, d]),
         "hw_batch_schedule_default": (None, [P(Schedule)]),
@@ -127,21 +129,26 @@ def _ptr(a):
 
 
 TIME_RULES = {"lobatto": 0, "gauss": 1}
+STEP_KERNELS = {"default": 0, "separate": 1, "fused": 2}
 
 
 def options(eq="advection", a=(1.0, 1.0), gamma_gas=1.4, cfl=0.5, gamma_lin=(0.94, 0.02, 0.02, 0.02), eps=1e-8,
-            positivity=False, time_rule="lobatto"):
+            positivity=False, time_rule="lobatto", step_kernels="default", inflow=None):
     o = Options()
     load().hw_options_default(ctypes.byref(o))
     o.eq = EQUATIONS[eq]
     o.positivity = int(bool(positivity))
     o.time_rule = TIME_RULES[time_rule]
+    o.step_kernels = STEP_KERNELS[step_kernels]
     o.ax, o.ay = a
     o.gamma_gas = gamma_gas
     o.cfl = cfl
     for k in range(4):
         o.gamma_lin[k] = gamma_lin[k]
     o.eps = eps
+    if inflow is not None:
+        for k, v in enumerate(np.asarray(inflow, dtype=np.float64).ravel()[:4]):
+            o.inflow[k] = v
     return o
 
 
@@ -180,6 +187,9 @@ class Mesh:
         self.src = mesh
         self.nt = mesh.nt
         self.h = hw_mesh_create(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, mesh.bc)
+        if getattr(mesh, "edge_bc", None) is not None:
+            self._ebc = np.ascontiguousarray(mesh.edge_bc, dtype=np.int32)
+            _check(load().hw_mesh_set_boundary(self.h, _ptr(self._ebc)))
 
     def neighbors(self):
         return hw_mesh_neighbors(self.h, self.nt)
@@ -307,6 +317,12 @@ class Solver:
                                       ctypes.c_void_p(pb.data_ptr() if pb is not None else None),
                                       ctypes.c_void_p(Ubar_next.data_ptr()), ctypes.c_void_p(Ubar_n.data_ptr()),
                                       ctypes.c_void_p(scratch.data_ptr()), scratch.numel()))
+
+    def step_kernels(self):
+        """'fused' or 'separate': the kernels this solver's steps run."""
+        p = ctypes.c_int32()
+        _check(load().hw_step_kernels(self.h, ctypes.byref(p)))
+        return "fused" if p.value == 2 else "separate"
 
     def profile(self, enable=True):
         _check(load().hw_profile(self.h, int(enable)))

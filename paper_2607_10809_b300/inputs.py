@@ -31,6 +31,8 @@ class Mesh:
     Lx: float = 0.0
     Ly: float = 0.0
     bc: int = 0
+    edge_bc: np.ndarray | None = None   # int32 [nt, 3]: type of local edge j where it is a boundary edge
+                                        # (1 transmissive, 2 reflective, 3 inflow); None: all transmissive
 
     @property
     def nt(self) -> int:
@@ -110,6 +112,81 @@ def jittered_box(n: int, L: float = 1.0, jitter: float = 0.15, seed: int = 0) ->
         xy += dx
     tri = _grid_triangles(n, n, lambda i, j: i * (n + 1) + j)
     return Mesh(xy=xy, tri=tri, Lx=0.0, Ly=0.0, bc=1)
+
+
+BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 1, 2, 3
+
+
+def jittered_rect(nx: int, ny: int, x0: float, x1: float, y0: float, y1: float, jitter: float = 0.15,
+                  seed: int = 0, periodic_x: bool = False) -> Mesh:
+    """[x0, x1] x [y0, y1] grid of nx x ny cells split by the "/" diagonal.
+    Interior vertices move by U(+-jitter h) per coordinate, boundary vertices
+    only along their side (corners stay); periodic_x: the left and right sides
+    are identified (x1 - x0 is the period)."""
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    rng = np.random.default_rng(seed)
+    ni = nx if periodic_x else nx + 1
+    I, J = np.meshgrid(np.arange(ni), np.arange(ny + 1), indexing="ij")
+    I = I.ravel(); J = J.ravel()
+    xy = np.stack([x0 + I * hx, y0 + J * hy], axis=1).astype(np.float64)
+    if jitter > 0:
+        d = rng.uniform(-1, 1, size=xy.shape) * jitter * np.array([hx, hy])
+        if not periodic_x:
+            d[(I == 0) | (I == nx), 0] = 0.0
+        d[(J == 0) | (J == ny), 1] = 0.0
+        xy += d
+    if periodic_x:
+        tri = _grid_triangles(nx, ny, lambda i, j: (i % nx) * (ny + 1) + j)
+    else:
+        tri = _grid_triangles(nx, ny, lambda i, j: i * (ny + 1) + j)
+    return Mesh(xy=xy, tri=tri, Lx=(x1 - x0) if periodic_x else 0.0, Ly=0.0, bc=1)
+
+
+def side_boundary_types(mesh: Mesh, left=BC_TRANSMISSIVE, right=BC_TRANSMISSIVE, bottom=BC_TRANSMISSIVE,
+                        top=BC_TRANSMISSIVE) -> np.ndarray:
+    """Per-edge boundary types [nt, 3] of an axis-aligned box mesh, each
+    boundary edge classified by the side its midpoint lies on."""
+    P = mesh.unwrapped()
+    lo, hi = P.reshape(-1, 2).min(axis=0), P.reshape(-1, 2).max(axis=0)
+    tol = 1e-9 * max(hi - lo)
+    ebc = np.full((mesh.nt, 3), BC_TRANSMISSIVE, dtype=np.int32)
+    for j in range(3):
+        mid = 0.5 * (P[:, j] + P[:, (j + 1) % 3])
+        for side, val in ((mid[:, 0] <= lo[0] + tol, left), (mid[:, 0] >= hi[0] - tol, right),
+                          (mid[:, 1] <= lo[1] + tol, bottom), (mid[:, 1] >= hi[1] - tol, top)):
+            ebc[side, j] = val
+    return ebc
+
+
+def lax_tube(seed: int = 0):
+    """The Lax shock tube of Section 3 on (-0.5, 0.5) x (-0.03, 0.03): a jittered
+    100 x 6 triangulation, inflow on the left (the left state), outflow on the
+    right, walls at the bottom and top; T = 0.16.  Returns (mesh, initial data
+    function, T, inflow state)."""
+    mesh = jittered_rect(100, 6, -0.5, 0.5, -0.03, 0.03, seed=seed)
+    mesh.edge_bc = side_boundary_types(mesh, left=BC_INFLOW, right=BC_TRANSMISSIVE, bottom=BC_REFLECTIVE,
+                                       top=BC_REFLECTIVE)
+    L, R = (0.445, 0.698, 0.0, 3.528), (0.5, 0.0, 0.0, 0.571)
+
+    def fn(x, y):
+        left = x < 0
+        return euler_from_primitive(np.where(left, L[0], R[0]), np.where(left, L[1], R[1]),
+                                    np.where(left, L[2], R[2]) + 0 * y, np.where(left, L[3], R[3]))
+    win = euler_from_primitive(*[np.array(v) for v in L])
+    return mesh, fn, 0.16, win
+
+
+def blast_waves(seed: int = 0):
+    """The interacting blast waves of Section 3 on (0, 1) x (-0.0075, 0.0075): a
+    jittered 400 x 6 triangulation with walls on all sides; T = 0.038."""
+    mesh = jittered_rect(400, 6, 0.0, 1.0, -0.0075, 0.0075, seed=seed)
+    mesh.edge_bc = side_boundary_types(mesh, BC_REFLECTIVE, BC_REFLECTIVE, BC_REFLECTIVE, BC_REFLECTIVE)
+
+    def fn(x, y):
+        p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0)) + 0 * y
+        one = np.ones_like(p)
+        return euler_from_primitive(one, 0 * one, 0 * one, p)
+    return mesh, fn, 0.038
 
 
 def poisson_disk_points(L: float, r: float, seed: int, attempts: int = 8) -> np.ndarray:

@@ -36,8 +36,10 @@ def riemann_batch(sizes, seed0):
     return meshes, states
 
 
-# seeds whose four-quadrant states the scheme with the scale limiter carries to T
-GOOD = [5, 6, 7, 8]
+# Four-quadrant states of the batched workload (solve k has the states of seed
+# 4 + k); solves 24, 30, 85 and 244 are among those whose first step loses
+# positivity with the scale limiter alone (the flux blending keeps them).
+C4_SOLVES = [24, 30, 85, 244]
 
 
 def test_batch_matches_oracle_per_solve_smooth_fp64():
@@ -69,10 +71,10 @@ SHOCK_TOL = 1e-11
 def test_batch_matches_oracle_per_solve_riemann_fp64():
     sizes = [6, 9, 12, 15]
     meshes, states = [], []
-    for n, sd in zip(sizes, GOOD):
-        mesh = I.jittered_box(n, seed=sd)
+    for n, k in zip(sizes, C4_SOLVES):
+        mesh = I.jittered_box(n, seed=4000 + k)
         meshes.append(mesh)
-        states.append(I.initial_state(mesh, I.quadrant_fn(I.quadrant_states(sd)), 4, nq=4))
+        states.append(I.initial_state(mesh, I.quadrant_fn(I.quadrant_states(4 + k)), 4, nq=4))
     T = 0.03
     b = hweno.Batch(meshes, states, eq="euler", precision="fp64", positivity=True)
     b.run_to(T)

@@ -111,19 +111,18 @@ def test_euler_vortex_2m_conserves_the_totals():
 # here all 256 solves run in one persistent launch (default schedule) and the
 # smallest and the largest solves are compared with the oracle.
 def batch_samples(meshes):
+    """The smallest, second smallest and largest solves, and solve 244, whose
+    first step loses positivity without the flux blending."""
     sizes = np.array([m.nt for m in meshes])
     order = np.argsort(sizes, kind="stable")
-    return [int(order[0]), int(order[1]), int(order[-1])]
+    return [int(order[0]), int(order[1]), int(order[-1]), 244]
 
 
 def test_batch_256_solves_sampled_fp64():
     meshes, states = I.config4_batch(256)
     T = 0.02
     b = hweno.Batch(meshes, states, eq="euler", precision="fp64", positivity=True)
-    try:
-        b.run_to(T)
-    except hweno.HwError as e:   # solves that blow up are isolated and reported
-        assert e.status == hweno.HW_ENONFINITE
+    b.run_to(T)
     for k in batch_samples(meshes):
         Ug, t, nsteps, failed = b.get_state(k)
         assert not failed and abs(t - T) < 1e-14
@@ -137,28 +136,20 @@ def test_batch_256_solves_sampled_fp64():
 
 
 def test_batch_256_solves_fp32_positivity_and_completion():
-    """The benchmark's batched run (FP32, scale limiter, T = 0.25): every solve
-    that is not reported failed reaches T with positive density and pressure
-    in every cell; the failed ones are a minority."""
+    """The benchmark's batched run (FP32, scale limiter and flux blending,
+    T = 0.25): every solve reaches T with positive density and pressure in
+    every cell."""
     meshes, states = I.config4_batch(256)
     T = 0.25
     b = hweno.Batch(meshes, states, eq="euler", precision="fp32", positivity=True)
-    try:
-        b.run_to(T)
-    except hweno.HwError as e:
-        assert e.status == hweno.HW_ENONFINITE
-    failed = 0
+    b.run_to(T)
     for k in range(len(meshes)):
         U, t, nsteps, f = b.get_state(k)
-        if f:
-            failed += 1
-            continue
+        assert not f, k
         assert abs(t - T) < 1e-12 and nsteps > 0
         rho = U[0, 0]
         p = 0.4 * (U[0, 3] - 0.5 * (U[0, 1] ** 2 + U[0, 2] ** 2) / rho)
         assert rho.min() > 0 and p.min() > 0, k
-    print(f"batched FP32 run: {len(meshes) - failed} of {len(meshes)} solves reached T = {T}, {failed} failed")
-    assert failed < len(meshes) // 10
     b.close()
 
 

@@ -184,6 +184,31 @@ def test_euler_riemann_with_scale_limiter(precision):
         assert np.all(err < 1e-3)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_euler_riemann_flux_blending(precision):
+    """The four-quadrant states of the batched workload's solve 244 on its own
+    8,192-triangle mesh: with the scale limiter alone the first step loses
+    positivity, so the flux blending is active from the first step.  The
+    single-solve kernels against the oracle, 12 steps."""
+    k = 244
+    mesh = I.jittered_box(I.config4_sizes(256)[k], seed=4000 + k)
+    U0 = I.initial_state(mesh, I.quadrant_fn(I.quadrant_states(4 + k)), 4, nq=4)
+    o = oracle.Oracle(mesh, "euler", positivity=True)
+    dts, U = [], U0
+    for _ in range(12):
+        dts.append(o.cfl_dt(U))
+        U = o.step(U, dts[-1])
+    s = hweno.Solver(mesh, U0, eq="euler", precision=precision, positivity=True)
+    for dt in dts:
+        s.step(dt)
+    Ug, t = s.get_state()
+    rho = Ug[0, 0]; p = 0.4 * (Ug[0, 3] - 0.5 * (Ug[0, 1] ** 2 + Ug[0, 2] ** 2) / rho)
+    assert rho.min() > 0 and p.min() > 0
+    err = rel_linf(Ug, U)
+    print(f"{precision} flux-blended Riemann, 12 steps: relative Linf {err:.2e}")
+    assert err < (FP64_TOL if precision == "fp64" else 1e-3)
+
+
 @pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
 def test_gauss_legendre_time_rule_matches_oracle(eq):
     """The two-node Gauss-Legendre time rule (a template variant of the edge

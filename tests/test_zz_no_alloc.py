@@ -55,8 +55,10 @@ def test_static_scratch_step_matches_hw_step_on_consecutive_calls(precision, cas
     mk_mesh, mk_state, opts = CASES[case]
     mesh = mk_mesh()
     U0 = mk_state(mesh)
-    ref = hweno.Solver(mesh, U0, eq="euler", precision=precision, **opts)
-    noalloc = hweno.Solver(mesh, U0, eq="euler", precision=precision, **opts)
+    # hw_step with the same two kernels (reconstruction, then flux) and the
+    # edge-point buffer in the caller's workspace
+    ref = hweno.Solver(mesh, U0, eq="euler", precision=precision, step_kernels="separate", **opts)
+    noalloc = hweno.Solver(mesh, U0, eq="euler", precision=precision, step_kernels="separate", **opts)
     for call in range(2):
         ref.step()
         noalloc.step_static_scratch()
