@@ -57,6 +57,7 @@ def lib():
         _lib.orc_lax_wendroff.argtypes = [ctypes.c_int, d, d, d, vp, vp]
         _lib.orc_cell_taylor.argtypes = [vp, vp, d, i64, vp]
         _lib.orc_flux_derivs.argtypes = [ctypes.c_int, d, d, d, vp, vp, vp, vp]
+        _lib.orc_step_cells.argtypes = [vp, vp, d, vp, i64, vp]
         _lib.orc_set_boundary.argtypes = [vp, vp]
         _lib.orc_set_inflow.argtypes = [vp, vp]
         _lib.orc_spectral_radius.argtypes = [ctypes.c_int, d, d, d, vp, d, d, vp]
@@ -138,6 +139,15 @@ class Oracle:
         if mask is not None:
             mk = np.ascontiguousarray(mask, dtype=np.uint8)
         _check(lib().orc_step(self._h, _ptr(U), dt, _ptr(out), _ptr(mk) if mk is not None else None))
+        return out
+
+    def step_cells(self, U, dt, cells):
+        """One step of the given cells only -> their new values [3, m, len(cells)]
+        (cells ascending; the cost grows with their number, not the mesh's)."""
+        U = self._u(U)
+        c = np.ascontiguousarray(np.sort(np.asarray(cells, dtype=np.int64)))
+        out = np.empty((3, self.m, c.size))
+        _check(lib().orc_step_cells(self._h, _ptr(U), float(dt), _ptr(c), c.size, _ptr(out)))
         return out
 
     def run_to(self, U, T, t0=0.0, max_steps=10 ** 9):

@@ -67,6 +67,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 namespace {
@@ -156,6 +157,7 @@ struct Problem {
   std::vector<std::array<int32_t, 3>> nbe;   // neighbour's local edge index
   std::vector<std::array<double, 6>> nbshift;  // (sx, sy) per local edge: nb frame + shift = own frame
   std::vector<EdgeRec> edges;
+  std::vector<std::array<int64_t, 3>> cell_edge;   // index in edges of local edge j of each cell
   std::vector<std::array<int, 3>> ebc;       // type of each boundary edge (R13, R25)
   double win[4] = {1.0, 0.0, 0.0, 2.5};      // state imposed at inflow edges (conservative)
   std::string err;
@@ -233,6 +235,7 @@ bool build_geometry(Problem& pb, const double* xy, const int32_t* tri) {
   }
   // periodic shift of each neighbour and the edge list (one record per edge)
   pb.ebc.assign(nt, {BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE});
+  pb.cell_edge.assign(nt, {-1, -1, -1});
   pb.nbshift.assign(nt, {0, 0, 0, 0, 0, 0});
   pb.edges.clear();
   for (int64_t t = 0; t < nt; ++t) {
@@ -257,6 +260,8 @@ bool build_geometry(Problem& pb, const double* xy, const int32_t* tri) {
         e.len = std::hypot(Bx - Ax, By - Ay);
         e.nx = (By - Ay) / e.len; e.ny = -(Bx - Ax) / e.len;
         e.sx = sx; e.sy = sy;
+        pb.cell_edge[t][j] = (int64_t)pb.edges.size();
+        if (u >= 0) pb.cell_edge[u][pb.nbe[t][j]] = (int64_t)pb.edges.size();
         pb.edges.push_back(e);
       }
     }
@@ -864,130 +869,158 @@ void flux_blend(const Problem& pb, const S* WL, const S* WR, const EdgeRec& e, S
     for (int c = 0; c < 4; ++c) Fe[c] = S(e.len) * (FL[c] + theta * (FH[c] - FL[c]));
 }
 
-// One time step.  If `mask` is non-null only cells with mask[i] != 0 are
-// updated (their stencils are reconstructed as needed); other entries of Unew
-// are copied from U.
+// One time step for the cells `targets` (ascending, all cells for a full
+// step): out[(k m + c) nout + r] = new value of (k, c) of targets[r].  Each
+// target's three edges are processed once per edge, in the order of the edge
+// list (an edge is formed when its first cell comes up), so a full step forms
+// every edge flux once, in the edge-list order.  The cost is proportional to
+// the number of targets.
+template <class S>
+int step_cells(const Problem& pb, const S* U, double dt, const std::vector<int64_t>& targets, S* out) {
+  const int m = pb.P.m;
+  const int64_t nout = (int64_t)targets.size();
+  const bool all = nout == pb.nt;
+  // positions of the targets and of the cells to reconstruct (targets and neighbours)
+  std::unordered_map<int64_t, int64_t> tpos, slot;
+  std::vector<int64_t> need;
+  auto tslot = [&](int64_t i) -> int64_t {
+    if (all) return i;
+    auto it = tpos.find(i);
+    return it == tpos.end() ? -1 : it->second;
+  };
+  if (!all) for (int64_t r = 0; r < nout; ++r) tpos[targets[r]] = r;
+  auto add_need = [&](int64_t i) {
+    if (all) return;
+    if (slot.emplace(i, (int64_t)need.size()).second) need.push_back(i);
+  };
+  for (int64_t i : targets) {
+    add_need(i);
+    for (int j = 0; j < 3; ++j) if (pb.nbr[i][j] >= 0) add_need(pb.nbr[i][j]);
+  }
+  auto rslot = [&](int64_t i) -> int64_t { return all ? i : slot.at(i); };
+  const int64_t nneed = all ? pb.nt : (int64_t)need.size();
+  std::vector<CellRecon<S>> rec(nneed * m);
+  for (int64_t k = 0; k < nneed; ++k) {
+    const int64_t i = all ? k : need[k];
+    for (int c = 0; c < m; ++c) {
+      rec[k * m + c] = reconstruct(pb, U, i, c);
+      if (!rec[k * m + c].ok) { g_err = "singular reconstruction system"; return 4; }
+    }
+    if (pb.P.positivity && pb.P.eq == EQ_EULER) {
+      positivity_scaling(pb, &rec[k * m], i);
+      positivity_time_scaling(pb, &rec[k * m], i, dt);
+    }
+  }
+  std::vector<S> Rf(nout * m, S(0.0)), GV(nout * m, S(0.0)), GY(nout * m, S(0.0));
+  for (int64_t i : targets)
+    for (int j = 0; j < 3; ++j) {
+      const EdgeRec& e = pb.edges[pb.cell_edge[i][j]];
+      // form the edge once: when its L cell comes up, or its R cell if L is not a target
+      if (!(e.L == i || tslot(e.L) < 0)) continue;
+      const int64_t sL = tslot(e.L), sR = e.R >= 0 ? tslot(e.R) : -1;
+      S Fe[4], Se[4];
+      for (int c = 0; c < m; ++c) { Fe[c] = S(0.0); Se[c] = S(0.0); }
+      // alpha from the cell averages of both sides (R10)
+      S WL[4], WR[4];
+      for (int c = 0; c < m; ++c) {
+        WL[c] = Uat(U, pb, 0, c, e.L);
+        WR[c] = Uat(U, pb, 0, c, e.R >= 0 ? e.R : e.L);
+      }
+      if (e.R < 0) {   // the ghost's average (R13, R25)
+        S gv[4], gy[4];
+        ghost_data(pb, U, e.L, e.jL, WR, gv, gy);
+      }
+      S alpha = smax(spectral_radius_n(pb.P, WL, e.nx, e.ny), spectral_radius_n(pb.P, WR, e.nx, e.ny));
+      for (int gi = 0; gi < 2; ++gi) {
+        double s = (gi == 0) ? 0.5 - kGL : 0.5 + kGL;
+        double x = e.Ax + s * (e.Bx - e.Ax), y = e.Ay + s * (e.By - e.Ay);
+        S Wi[4], Wti[4], Wtti[4], We[4], Wte[4], Wtte[4];
+        side_taylor(pb, rec.data() + rslot(e.L) * m, x, y, Wi, Wti, Wtti);
+        if (e.R >= 0) {
+          side_taylor(pb, rec.data() + rslot(e.R) * m, x - e.sx, y - e.sy, We, Wte, Wtte);
+        } else {
+          // boundary: the ghost's Taylor data at the edge point (R13, R25)
+          const int type = pb.ebc[e.L][e.jL];
+          if (type == BC_INFLOW) {
+            for (int c = 0; c < m; ++c) { We[c] = S(pb.win[c]); Wte[c] = S(0.0); Wtte[c] = S(0.0); }
+          } else if (type == BC_REFLECTIVE && pb.P.eq == EQ_EULER) {
+            mirror_state(e.nx, e.ny, Wi, We);      // the mirrored solution at a point of the wall
+            mirror_state(e.nx, e.ny, Wti, Wte);
+            mirror_state(e.nx, e.ny, Wtti, Wtte);
+          } else {
+            for (int c = 0; c < m; ++c) { We[c] = Wi[c]; Wte[c] = Wti[c]; Wtte[c] = Wtti[c]; }
+          }
+        }
+        // Eqs. tay / tayext at the time nodes, LLF flux, time quadrature (Eq. flux)
+        const bool gauss = pb.P.time_rule == 1;
+        for (int si = 0; si < (gauss ? 2 : 3); ++si) {
+          double tau = (gauss ? kTauGL[si] : kTau[si]) * dt;
+          S a[4], b[4], Ha[4], Hb[4];
+          for (int c = 0; c < m; ++c) {
+            a[c] = Wi[c] + Wti[c] * S(tau) + Wtti[c] * S(0.5 * tau * tau);
+            b[c] = We[c] + Wte[c] * S(tau) + Wtte[c] * S(0.5 * tau * tau);
+          }
+          flux_normal(pb.P, a, e.nx, e.ny, Ha);
+          flux_normal(pb.P, b, e.nx, e.ny, Hb);
+          for (int c = 0; c < m; ++c) {
+            S H = S(0.5) * (Hb[c] + Ha[c] - alpha * (b[c] - a[c]));
+            Fe[c] = Fe[c] + S((gauss ? kWtGL[si] : kWt[si]) * 0.5 * e.len) * H;  // w_s * w_G * |e|
+          }
+          if (!gauss && si == 2) {
+            // Eq. timeflux: central value at t_{n+1} (Lobatto node tau = dt)
+            for (int c = 0; c < m; ++c) Se[c] = Se[c] + S(0.5 * e.len) * (S(0.5) * (a[c] + b[c]));
+          }
+        }
+        if (gauss) {
+          // Eq. timeflux: the central value at t_{n+1} from its own Taylor evaluation
+          S a[4], b[4];
+          for (int c = 0; c < m; ++c) {
+            a[c] = Wi[c] + Wti[c] * S(dt) + Wtti[c] * S(0.5 * dt * dt);
+            b[c] = We[c] + Wte[c] * S(dt) + Wtte[c] * S(0.5 * dt * dt);
+            Se[c] = Se[c] + S(0.5 * e.len) * (S(0.5) * (a[c] + b[c]));
+          }
+        }
+      }
+      if (pb.P.positivity == 1 && pb.P.eq == EQ_EULER) flux_blend(pb, WL, WR, e, alpha, dt, Fe);
+      for (int c = 0; c < m; ++c) {
+        if (sL >= 0) {
+          Rf[sL * m + c] = Rf[sL * m + c] + Fe[c];
+          GV[sL * m + c] = GV[sL * m + c] + Se[c] * S(e.nx);
+          GY[sL * m + c] = GY[sL * m + c] + Se[c] * S(e.ny);
+        }
+        if (sR >= 0) {
+          Rf[sR * m + c] = Rf[sR * m + c] - Fe[c];
+          GV[sR * m + c] = GV[sR * m + c] - Se[c] * S(e.nx);
+          GY[sR * m + c] = GY[sR * m + c] - Se[c] * S(e.ny);
+        }
+      }
+      }
+  // Eq. flx and Eq. derave2d2
+  for (int64_t r = 0; r < nout; ++r) {
+    const int64_t i = targets[r];
+    for (int c = 0; c < m; ++c) {
+      out[(0 * m + c) * nout + r] = Uat(U, pb, 0, c, i) - S(dt / pb.area[i]) * Rf[r * m + c];
+      out[(1 * m + c) * nout + r] = GV[r * m + c] / S(pb.area[i]);
+      out[(2 * m + c) * nout + r] = GY[r * m + c] / S(pb.area[i]);
+    }
+  }
+  return 0;
+}
+
+// One time step of all cells, or (mask non-null) of the cells with
+// mask[i] != 0, whose new values are written while the others are copied.
 template <class S> int step_impl(const Problem& pb, const S* U, double dt, S* Unew, const uint8_t* mask) {
   const int m = pb.P.m;
   const int64_t nt = pb.nt;
-  // cells to reconstruct
-  std::vector<uint8_t> need(nt, mask ? 0 : 1);
-  if (mask) {
-    for (int64_t i = 0; i < nt; ++i)
-      if (mask[i]) {
-        need[i] = 1;
-        for (int j = 0; j < 3; ++j) if (pb.nbr[i][j] >= 0) need[pb.nbr[i][j]] = 1;
-      }
-  }
-  // reconstructions of the needed cells, stored compactly (slot[i] -> position)
-  std::vector<int64_t> slot(nt, -1);
-  int64_t nneed = 0;
-  for (int64_t i = 0; i < nt; ++i) if (need[i]) slot[i] = nneed++;
-  std::vector<CellRecon<S>> rec(nneed * m);
-  for (int64_t i = 0; i < nt; ++i) {
-    if (!need[i]) continue;
-    for (int c = 0; c < m; ++c) {
-      rec[slot[i] * m + c] = reconstruct(pb, U, i, c);
-      if (!rec[slot[i] * m + c].ok) { g_err = "singular reconstruction system"; return 4; }
-    }
-    if (pb.P.positivity && pb.P.eq == EQ_EULER) {
-      positivity_scaling(pb, &rec[slot[i] * m], i);
-      positivity_time_scaling(pb, &rec[slot[i] * m], i, dt);
-    }
-  }
-  std::vector<S> Rf(nt * m, S(0.0)), GV(nt * m, S(0.0)), GY(nt * m, S(0.0));
-  for (const EdgeRec& e : pb.edges) {
-    bool useL = !mask || mask[e.L];
-    bool useR = e.R >= 0 && (!mask || mask[e.R]);
-    if (!useL && !useR) continue;
-    S Fe[4], Se[4];
-    for (int c = 0; c < m; ++c) { Fe[c] = S(0.0); Se[c] = S(0.0); }
-    // alpha from the cell averages of both sides (R10)
-    S WL[4], WR[4];
-    for (int c = 0; c < m; ++c) {
-      WL[c] = Uat(U, pb, 0, c, e.L);
-      WR[c] = Uat(U, pb, 0, c, e.R >= 0 ? e.R : e.L);
-    }
-    if (e.R < 0) {   // the ghost's average (R13, R25)
-      S gv[4], gy[4];
-      ghost_data(pb, U, e.L, e.jL, WR, gv, gy);
-    }
-    S alpha = smax(spectral_radius_n(pb.P, WL, e.nx, e.ny), spectral_radius_n(pb.P, WR, e.nx, e.ny));
-    for (int gi = 0; gi < 2; ++gi) {
-      double s = (gi == 0) ? 0.5 - kGL : 0.5 + kGL;
-      double x = e.Ax + s * (e.Bx - e.Ax), y = e.Ay + s * (e.By - e.Ay);
-      S Wi[4], Wti[4], Wtti[4], We[4], Wte[4], Wtte[4];
-      side_taylor(pb, rec.data() + slot[e.L] * m, x, y, Wi, Wti, Wtti);
-      if (e.R >= 0) {
-        side_taylor(pb, rec.data() + slot[e.R] * m, x - e.sx, y - e.sy, We, Wte, Wtte);
-      } else {
-        // boundary: the ghost's Taylor data at the edge point (R13, R25)
-        const int type = pb.ebc[e.L][e.jL];
-        if (type == BC_INFLOW) {
-          for (int c = 0; c < m; ++c) { We[c] = S(pb.win[c]); Wte[c] = S(0.0); Wtte[c] = S(0.0); }
-        } else if (type == BC_REFLECTIVE && pb.P.eq == EQ_EULER) {
-          mirror_state(e.nx, e.ny, Wi, We);      // the mirrored solution at a point of the wall
-          mirror_state(e.nx, e.ny, Wti, Wte);
-          mirror_state(e.nx, e.ny, Wtti, Wtte);
-        } else {
-          for (int c = 0; c < m; ++c) { We[c] = Wi[c]; Wte[c] = Wti[c]; Wtte[c] = Wtti[c]; }
-        }
-      }
-      // Eqs. tay / tayext at the time nodes, LLF flux, time quadrature (Eq. flux)
-      const bool gauss = pb.P.time_rule == 1;
-      for (int si = 0; si < (gauss ? 2 : 3); ++si) {
-        double tau = (gauss ? kTauGL[si] : kTau[si]) * dt;
-        S a[4], b[4], Ha[4], Hb[4];
-        for (int c = 0; c < m; ++c) {
-          a[c] = Wi[c] + Wti[c] * S(tau) + Wtti[c] * S(0.5 * tau * tau);
-          b[c] = We[c] + Wte[c] * S(tau) + Wtte[c] * S(0.5 * tau * tau);
-        }
-        flux_normal(pb.P, a, e.nx, e.ny, Ha);
-        flux_normal(pb.P, b, e.nx, e.ny, Hb);
-        for (int c = 0; c < m; ++c) {
-          S H = S(0.5) * (Hb[c] + Ha[c] - alpha * (b[c] - a[c]));
-          Fe[c] = Fe[c] + S((gauss ? kWtGL[si] : kWt[si]) * 0.5 * e.len) * H;  // w_s * w_G * |e|
-        }
-        if (!gauss && si == 2) {
-          // Eq. timeflux: central value at t_{n+1} (Lobatto node tau = dt)
-          for (int c = 0; c < m; ++c) Se[c] = Se[c] + S(0.5 * e.len) * (S(0.5) * (a[c] + b[c]));
-        }
-      }
-      if (gauss) {
-        // Eq. timeflux: the central value at t_{n+1} from its own Taylor evaluation
-        S a[4], b[4];
-        for (int c = 0; c < m; ++c) {
-          a[c] = Wi[c] + Wti[c] * S(dt) + Wtti[c] * S(0.5 * dt * dt);
-          b[c] = We[c] + Wte[c] * S(dt) + Wtte[c] * S(0.5 * dt * dt);
-          Se[c] = Se[c] + S(0.5 * e.len) * (S(0.5) * (a[c] + b[c]));
-        }
-      }
-    }
-    if (pb.P.positivity == 1 && pb.P.eq == EQ_EULER) flux_blend(pb, WL, WR, e, alpha, dt, Fe);
-    for (int c = 0; c < m; ++c) {
-      Rf[e.L * m + c] = Rf[e.L * m + c] + Fe[c];
-      GV[e.L * m + c] = GV[e.L * m + c] + Se[c] * S(e.nx);
-      GY[e.L * m + c] = GY[e.L * m + c] + Se[c] * S(e.ny);
-      if (e.R >= 0) {
-        Rf[e.R * m + c] = Rf[e.R * m + c] - Fe[c];
-        GV[e.R * m + c] = GV[e.R * m + c] - Se[c] * S(e.nx);
-        GY[e.R * m + c] = GY[e.R * m + c] - Se[c] * S(e.ny);
-      }
-    }
-  }
-  // Eq. flx and Eq. derave2d2
-  for (int64_t i = 0; i < nt; ++i) {
-    bool upd = !mask || mask[i];
-    for (int c = 0; c < m; ++c) {
-      if (upd) {
-        Unew[(0 * m + c) * nt + i] = Uat(U, pb, 0, c, i) - S(dt / pb.area[i]) * Rf[i * m + c];
-        Unew[(1 * m + c) * nt + i] = GV[i * m + c] / S(pb.area[i]);
-        Unew[(2 * m + c) * nt + i] = GY[i * m + c] / S(pb.area[i]);
-      } else {
-        for (int k = 0; k < 3; ++k) Unew[(k * m + c) * nt + i] = Uat(U, pb, k, c, i);
-      }
-    }
-  }
+  std::vector<int64_t> targets;
+  for (int64_t i = 0; i < nt; ++i) if (!mask || mask[i]) targets.push_back(i);
+  std::vector<S> out(3 * m * targets.size());
+  const int rc = step_cells(pb, U, dt, targets, out.data());
+  if (rc) return rc;
+  if (mask) std::copy(U, U + 3 * m * nt, Unew);
+  const int64_t nout = (int64_t)targets.size();
+  for (int k = 0; k < 3 * m; ++k)
+    for (int64_t r = 0; r < nout; ++r) Unew[k * nt + targets[r]] = out[k * nout + r];
   return 0;
 }
 
@@ -1091,6 +1124,13 @@ double orc_cfl_dt(const orc_problem* p, const double* U) { return cfl_dt(*reinte
 
 int orc_step(const orc_problem* p, const double* U, double dt, double* Unew, const uint8_t* mask) {
   return step_impl<double>(*reinterpret_cast<const Problem*>(p), U, dt, Unew, mask);
+}
+
+// One step of the cells `cells` only (ascending caller indices): out[3][m][n]
+// receives their new values.  The cost grows with n, not with the mesh.
+int orc_step_cells(const orc_problem* p, const double* U, double dt, const int64_t* cells, int64_t n, double* out) {
+  std::vector<int64_t> t(cells, cells + n);
+  return step_cells<double>(*reinterpret_cast<const Problem*>(p), U, dt, t, out);
 }
 
 // Run from t0 to T with the CFL time step (R12).  U is updated in place.

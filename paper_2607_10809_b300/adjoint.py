@@ -4,7 +4,9 @@ the C ABI (hw_step_adjoint) and checkpointing every `every` steps.
 
 The time steps are held fixed (they are inputs, not differentiated).  The
 backward pass restores each checkpoint, recomputes the states of its segment
-and runs the adjoint steps of the segment in reverse."""
+and runs the adjoint steps of the segment in reverse.  The last segment is
+not recomputed: the forward pass keeps its states and edge-point data (the
+backward pass starts with it)."""
 from __future__ import annotations
 
 import numpy as np
@@ -24,17 +26,25 @@ class Rollout(torch.autograd.Function):
         s.host_to_internal(np.asarray(U0.detach().cpu().numpy(), dtype=np.float64), buf)
         s.import_state(buf, 0.0)
         ckpts, times, t = [], [], 0.0
+        last = (len(dts) - 1) // every * every if len(dts) else 0   # first step of the last segment
+        states = [s.state_buffer() for _ in range(every)]
+        pbs = [s.pb_buffer() for _ in range(every)]
         for k, dt in enumerate(dts):
             if k % every == 0:
                 c = s.state_buffer()
                 s.export_state(c)
                 ckpts.append(c)
                 times.append(t)
-            s.step(float(dt))
+            if k >= last:   # keep the last segment's states and edge-point data
+                s.export_state(states[k - last])
+                s.step_keep(float(dt), pbs[k - last])
+            else:
+                s.step(float(dt))
             t += float(dt)
         UT = _host_tensor(U0.shape)
         s.get_state(out=UT.numpy())
         ctx.solver, ctx.dts, ctx.every, ctx.ckpts, ctx.times = s, list(dts), every, ckpts, times
+        ctx.states, ctx.pbs = states, pbs
         return UT
 
     @staticmethod
@@ -44,14 +54,14 @@ class Rollout(torch.autograd.Function):
         s.host_to_internal(np.asarray(gUT.detach().cpu().numpy(), dtype=np.float64), ub)
         ubn = s.state_buffer()
         scratch = s.adjoint_scratch()
-        states = [s.state_buffer() for _ in range(every)]
-        pbs = [s.pb_buffer() for _ in range(every)]
+        states, pbs = ctx.states, ctx.pbs
         for seg in reversed(range(len(ctx.ckpts))):
             start, end = seg * every, min((seg + 1) * every, len(dts))
-            s.import_state(ctx.ckpts[seg], ctx.times[seg])
-            for k in range(start, end):          # recompute the segment's states and edge-point data
-                s.export_state(states[k - start])
-                s.step_keep(float(dts[k]), pbs[k - start])
+            if seg < len(ctx.ckpts) - 1:         # the last segment's data are still in the buffers
+                s.import_state(ctx.ckpts[seg], ctx.times[seg])
+                for k in range(start, end):      # recompute the segment's states and edge-point data
+                    s.export_state(states[k - start])
+                    s.step_keep(float(dts[k]), pbs[k - start])
             for k in reversed(range(start, end)):
                 s.step_adjoint(float(dts[k]), states[k - start], ub, ubn, scratch, pbs[k - start])
                 ub, ubn = ubn, ub

@@ -31,7 +31,7 @@ hw_status bfail(hw_status s, const std::string& msg) {
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct BatchLayout {
-  size_t rgeo, igeo, U0, U1, Uinit, Pb, perm, stage, tiles, bs, bs_init, ctl, total;
+  size_t rgeo, igeo, U0, U1, Uinit, Pb, comp, comp_bytes, perm, stage, tiles, bs, bs_init, ctl, total;
 };
 
 struct Plan {
@@ -67,6 +67,9 @@ BatchLayout make_batch_layout(const Plan& p, int n, int m, int prec) {
   L.U1 = take((size_t)3 * m * ld * s);
   L.Uinit = take((size_t)3 * m * ld * s);
   L.Pb = take((size_t)18 * m * ld * s);
+  // FP32: compensation words of the cell averages (compensated summation of the updates)
+  L.comp_bytes = prec == HW_FP32 ? (size_t)m * ld * 4 : 0;
+  L.comp = take(L.comp_bytes);
   L.perm = take(ld * 4);
   L.stage = take((size_t)3 * m * p.maxnt * 8);
   L.tiles = take((size_t)p.ntiles * sizeof(int4));
@@ -115,6 +118,7 @@ struct hw_batch {
     a.U0 = ws + L.U0;
     a.U1 = ws + L.U1;
     a.Pb = ws + L.Pb;
+    a.C = L.comp_bytes ? ws + L.comp : nullptr;
     a.maps = &maps;
     a.tiles = reinterpret_cast<const int4*>(ws + L.tiles);
     a.ntiles = plan.ntiles;
@@ -204,6 +208,7 @@ hw_status restore_initial(hw_batch* b) {
   HB_CUDA(cudaMemcpyAsync(b->ws + b->L.U0, b->ws + b->L.Uinit, sz, cudaMemcpyDeviceToDevice, b->stream));
   HB_CUDA(cudaMemcpyAsync(b->ws + b->L.bs, b->ws + b->L.bs_init, b->n * sizeof(BatchSolve), cudaMemcpyDeviceToDevice,
                           b->stream));
+  if (b->L.comp_bytes) HB_CUDA(cudaMemsetAsync(b->ws + b->L.comp, 0, b->L.comp_bytes, b->stream));
   return HW_OK;
 }
 }  // namespace
@@ -313,6 +318,7 @@ hw_status hw_batch_create(const hw_mesh* const* meshes, int32_t n, const hw_opti
     HB_CUDA(cudaGetLastError());
   }
   HB_CUDA(cudaMemcpyAsync(b->ws + b->L.Uinit, b->ws + b->L.U0, 3 * m * ld * es, cudaMemcpyDeviceToDevice, b->stream));
+  if (b->L.comp_bytes) HB_CUDA(cudaMemsetAsync(b->ws + b->L.comp, 0, b->L.comp_bytes, b->stream));
   // per-solve state: t = 0, CFL step
   std::vector<BatchSolve> bs0(n);
   for (auto& x : bs0) {
@@ -444,7 +450,8 @@ hw_status hw_batch_get_state(hw_batch* b, int32_t solve, double* Wbar, double* V
   const size_t nt = (size_t)b->plan.nt[solve], off = (size_t)b->plan.off[solve];
   const char* U = b->ws + ((x.nsteps & 1) ? b->L.U1 : b->L.U0) + off * 3 * m * es;
   double* stage = reinterpret_cast<double*>(b->ws + b->L.stage);
-  launch_gather(b->prec, U, nullptr, (int)m, reinterpret_cast<const int32_t*>(b->ws + b->L.perm) + off, (int)nt, 0,
+  const char* Cw = b->L.comp_bytes ? b->ws + b->L.comp + off * m * 4 : nullptr;   // FP32 compensation words
+  launch_gather(b->prec, U, Cw, (int)m, reinterpret_cast<const int32_t*>(b->ws + b->L.perm) + off, (int)nt, 0,
                 (int)(3 * m),
                 stage, b->stream);
   HB_CUDA(cudaGetLastError());

@@ -153,7 +153,8 @@ template <typename R> struct SingleCtx {
 template <typename R> struct BatchCtx {
   const int4* tiles;   // (first cell, count, solve, 0)
   int nt;
-  __device__ __forceinline__ R* comp(int) const { return nullptr; }   // batched solves: plain updates
+  R* C;                // FP32: compensation words of the cell averages (compensated updates), or nullptr
+  __device__ __forceinline__ R* comp(int) const { return C; }
   BatchSolve* bs;
   BatchCtl* ctl;
   R* U0;
@@ -809,9 +810,11 @@ __global__ void __launch_bounds__(LIM ? kThreads : kLeanThreads) k_recon(const _
 }
 
 // Resident blocks per SM the flux kernel is compiled for (register budget):
-// FP32 Euler takes HW_EDGE_MIN_BLOCKS (measured best), the rest the default.
+// FP32 Euler takes HW_EDGE_MIN_BLOCKS (4: 72 registers, no spills; the
+// boundary-ghost branches would otherwise raise it to 95 and cost a block per
+// SM), the rest the compiler's choice.
 #ifndef HW_EDGE_MIN_BLOCKS
-#define HW_EDGE_MIN_BLOCKS 1
+#define HW_EDGE_MIN_BLOCKS 4
 #endif
 template <typename R, int EQ> constexpr int edge_min_blocks() {
   return (sizeof(R) == 4 && EQ == kEqEuler) ? HW_EDGE_MIN_BLOCKS : 1;
@@ -1091,8 +1094,14 @@ __device__ bool grid_barrier(BatchCtl* ctl, unsigned long long spin_limit, bool 
 // the flux/update phase (per-solve CFL minima), a barrier, the per-solve time
 // step / status update, a barrier.  Leaves when no solve is running or after
 // max_steps steps.
+// Resident blocks per SM of the batched kernel (register budget), FP32.
+#ifndef HW_BATCH_MIN_BLOCKS
+#define HW_BATCH_MIN_BLOCKS 3
+#endif
+template <typename R> constexpr int batch_min_blocks() { return sizeof(R) == 4 ? HW_BATCH_MIN_BLOCKS : 1; }
+
 template <typename R, int EQ, bool LIM>
-__global__ void __launch_bounds__(kThreads) k_batch(const __grid_constant__ CUtensorMap mGeo,
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<R>()) k_batch(const __grid_constant__ CUtensorMap mGeo,
                                                      const __grid_constant__ CUtensorMap mEgeo,
                                                      const __grid_constant__ CUtensorMap mIdx,
                                                      const __grid_constant__ CUtensorMap mLgeo, R* U0, R* U1,
@@ -1472,7 +1481,8 @@ template <typename R, int EQ, bool LIM> int batch_cap_t() {
   return cap;
 }
 template <typename R, int EQ, bool LIM> cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t st) {
-  BatchCtx<R> ctx{a.tiles, a.ntiles, a.bs, a.ctl, reinterpret_cast<R*>(a.U0), reinterpret_cast<R*>(a.U1)};
+  BatchCtx<R> ctx{a.tiles, a.ntiles, reinterpret_cast<R*>(a.C), a.bs, a.ctl, reinterpret_cast<R*>(a.U0),
+                  reinterpret_cast<R*>(a.U1)};
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(a.grid);
   cfg.blockDim = dim3(kThreads);

@@ -101,6 +101,7 @@ struct BatchArgs {
   void* U0;                 // state buffer 0 [ld][3m]
   void* U1;                 // state buffer 1
   void* Pb;                 // edge-point buffer [ld][6][3][m]
+  void* C;                  // FP32: compensation words of the cell averages [ld][m]; nullptr: none
   const TensorMaps* maps;
   const int4* tiles;        // (first cell, count, solve, 0)
   int ntiles;

@@ -827,3 +827,21 @@ def test_lax_tube_against_the_exact_riemann_solution():
     print(f"Lax tube: {len(dts)} steps, density L1 error {l1:.3e}, mean |v| {mean_v:.2e}")
     assert l1 < 0.02
     assert mean_v < 0.01     # the jittered cells perturb the flow at the shock; the walls keep it 1D
+
+
+def test_step_of_a_patch_equals_the_full_step_there():
+    """The patch step (used to time the oracle) gives the full step's values on
+    its cells; the full step is unchanged by the patch path."""
+    mesh = I.jittered_periodic(16, 10.0, 0.15, seed=5)
+    U = I.initial_state(mesh, I.vortex, 4)
+    o = oracle.Oracle(mesh, "euler")
+    dt = o.cfl_dt(U)
+    full = o.step(U, dt)
+    cells = np.arange(40, 260, 3)
+    part = o.step_cells(U, dt, cells)
+    np.testing.assert_allclose(part, full[:, :, cells], rtol=1e-13, atol=1e-13 * np.abs(full).max())
+    mask = np.zeros(mesh.nt, np.uint8); mask[cells] = 1
+    masked = o.step(U, dt, mask=mask)
+    np.testing.assert_array_equal(masked[:, :, cells], part)
+    others = np.setdiff1d(np.arange(mesh.nt), cells)
+    np.testing.assert_array_equal(masked[:, :, others], U[:, :, others])
