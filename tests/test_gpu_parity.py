@@ -205,8 +205,15 @@ def test_euler_riemann_flux_blending(precision):
     rho = Ug[0, 0]; p = 0.4 * (Ug[0, 3] - 0.5 * (Ug[0, 1] ** 2 + Ug[0, 2] ** 2) / rho)
     assert rho.min() > 0 and p.min() > 0
     err = rel_linf(Ug, U)
-    print(f"{precision} flux-blended Riemann, 12 steps: relative Linf {err:.2e}")
-    assert err < (FP64_TOL if precision == "fp64" else 1e-3)
+    area = I.cell_areas(mesh)
+    l1 = ((np.abs(Ug - U) * area).sum(axis=-1) / np.maximum((np.abs(U) * area).sum(axis=-1), 1e-300)).max()
+    print(f"{precision} flux-blended Riemann, 12 steps: relative Linf {err:.2e}, relative L1 {l1:.2e}")
+    if precision == "fp64":
+        # shocked, limited data: the parity norm of R24 (relative L1 1e-12,
+        # relative Linf 1e-10); rounding is amplified in a few cells at the jumps
+        assert l1 < FP64_TOL and err < 1e-10
+    else:
+        assert err < 1e-3
 
 
 @pytest.mark.parametrize("eq", ["advection", "burgers", "euler"])
