@@ -835,13 +835,9 @@ template <class S> void positivity_time_scaling(const Problem& pb, CellRecon<S>*
 // that keeps Phi_e admissible on both sides of the edge (the scale limiter's
 // fraction along the segment from Phi_e(0) to Phi_e(1)).  Both sides use the
 // same theta, so the update stays conservative.  Fe is the high-order edge
-// flux times |e| on entry and the blended one on exit; Se, the edge's
-// Green-Gauss central value times |e|, is blended with the same theta toward
-// the first-order central value (the mean of the two averages), so that the
-// derivative averages stay consistent with the averages' update.
+// flux times |e| on entry and the blended one on exit.
 template <class S>
-void flux_blend(const Problem& pb, const S* WL, const S* WR, const EdgeRec& e, S alpha, double dt, S Fe[4],
-                S Se[4]) {
+void flux_blend(const Problem& pb, const S* WL, const S* WR, const EdgeRec& e, S alpha, double dt, S Fe[4]) {
   const double gam = pb.P.gam;
   S HL[4], HR[4], FL[4], FH[4];
   flux_normal(pb.P, WL, e.nx, e.ny, HL);
@@ -870,12 +866,7 @@ void flux_blend(const Problem& pb, const S* WL, const S* WR, const EdgeRec& e, S
     if (val(th) < val(theta)) theta = th;
   }
   if (val(theta) < 1.0)
-    for (int c = 0; c < 4; ++c) {
-      Fe[c] = S(e.len) * (FL[c] + theta * (FH[c] - FL[c]));
-      // the Green-Gauss central value follows the same blend toward the
-      // first-order one, the mean of the two averages
-      Se[c] = theta * Se[c] + (S(1.0) - theta) * S(e.len) * S(0.5) * (WL[c] + WR[c]);
-    }
+    for (int c = 0; c < 4; ++c) Fe[c] = S(e.len) * (FL[c] + theta * (FH[c] - FL[c]));
 }
 
 // One time step for the cells `targets` (ascending, all cells for a full
@@ -990,7 +981,7 @@ int step_cells(const Problem& pb, const S* U, double dt, const std::vector<int64
           }
         }
       }
-      if (pb.P.positivity == 1 && pb.P.eq == EQ_EULER) flux_blend(pb, WL, WR, e, alpha, dt, Fe, Se);
+      if (pb.P.positivity == 1 && pb.P.eq == EQ_EULER) flux_blend(pb, WL, WR, e, alpha, dt, Fe);
       for (int c = 0; c < m; ++c) {
         if (sL >= 0) {
           Rf[sL * m + c] = Rf[sL * m + c] + Fe[c];

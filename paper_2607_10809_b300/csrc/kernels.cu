@@ -646,13 +646,8 @@ __device__ __forceinline__ void flux_update_block(Ctx& ctx, int tile, int cell0,
         const R lamR = nb >= 0 ? dtr * (left ? pnb : pown) : R(-1);
         const R theta = blend_theta(EqC<R>::gam(P), WL, WR, HL, HR, FL, FH, lamL, lamR);
         if (theta < R(1)) {
-          // the Green-Gauss central value follows the same blend toward the
-          // first-order one (the mean of the two averages)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            Fe[c] = FL[c] + theta * (Fe[c] - FL[c]);
-            Sh[c] = theta * Sh[c] + (R(1) - theta) * (R(0.5) * (WL[c] + WR[c]));
-          }
+          for (int c = 0; c < 4; ++c) Fe[c] = FL[c] + theta * (Fe[c] - FL[c]);
         }
       }
       __syncthreads();
