@@ -64,11 +64,10 @@ def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
 # dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
 # it was measured on; it is reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources_sha": "4b85f4c1086c601f",
+    "sources_sha": "82a59367907bd6eb",
     # full-size (1,999,928-cell) single-pass ncu capture, per cell
-    "per_cell": {"recon_fp32": 634.3, "edge_fp32": 467.2, "recon_fp64": 1277.5, "edge_fp64": 872.1},
+    "per_cell": {"recon_fp32": 633.5, "edge_fp32": 467.2},
 }
-
 
 # Floating-point operations per cell and launch (FMA counted as 2), from the
 # executed-instruction counters of one ncu capture of the 499,942-cell vortex
@@ -76,9 +75,10 @@ TRAFFIC = {
 # valid for the sources hash of TRAFFIC.
 FLOPS = {"recon_fp64": 4382, "edge_fp64": 2932, "recon_fp32": 3986, "edge_fp32": 2609}
 
-# FP64 FMA throughput of this B300 per SM clock: the ALU probe
-# (paper_2607_10809_b300/probes/alu_peaks.cu) measured 1.132 TFLOP/s at 1935 MHz.
-FP64_FLOP_PER_CLOCK = 1.132e12 / 1935e6
+# FP64 peak of the B300 per SM clock: the nominal 1.25 TFLOP/s at the 2032 MHz
+# maximum clock is 2 FP64 FMA per SM per clock on 148 SMs (a one-off FMA probe
+# measured 1.132 TFLOP/s at 1935 MHz, the same rate per clock).
+FP64_FLOP_PER_CLOCK = 148 * 2 * 2
 
 
 def kernel_sources_sha() -> str:
@@ -446,7 +446,7 @@ def fp64_roofline(N, rec_ms, edge_ms, clocks, sha):
     peak = FP64_FLOP_PER_CLOCK * clocks["sm_mhz"] * 1e6 / 1e12 if clocks.get("sm_mhz") else None
     return {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "flop_per_cell": FLOPS[f"{dom}_fp64"],
-            "peak_kind": "FP64 FMA probe scaled to the sampled SM clock"}
+            "peak_kind": "2 FP64 FMA per SM per clock (nominal 1.25 TFLOP/s at 2032 MHz) at the sampled SM clock"}
 
 
 # ---------------------------------------------------------------- batched leg

@@ -13,6 +13,7 @@
 
 #include "../../include/hweno.h"
 #include "internal.h"
+#include "nvtx.h"
 #include "kernels.h"
 
 using namespace hw;
@@ -264,6 +265,7 @@ void hw_options_default(hw_options* o) {
 
 hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, int64_t ntri, double Lx, double Ly,
                          int32_t bc, hw_mesh** out) {
+  hw::NvtxRange nvtx_("hw_mesh_create");
   if (!xy || !tri || !out || nvert <= 0 || ntri <= 0) return fail(HW_EINVAL, "null pointer or empty mesh");
   if (bc != HW_BC_PERIODIC && bc != HW_BC_TRANSMISSIVE) return fail(HW_EINVAL, "unknown boundary condition");
   hw_mesh* h = new (std::nothrow) hw_mesh();
@@ -350,6 +352,7 @@ static hw_status upload_state(hw_solver* s, const double* W, const double* V, co
 hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t precision, const double* Wbar,
                         const double* Vbar, const double* Ybar, void* workspace, size_t workspace_bytes,
                         void* cuda_stream, hw_solver** out) {
+  hw::NvtxRange nvtx_("hw_state_init");
   if (!mesh || !Wbar || !Vbar || !Ybar || !workspace || !out) return fail(HW_EINVAL, "null pointer");
   if (hw_status st = check_options(opt)) return st;
   if (precision != HW_FP64 && precision != HW_FP32) return fail(HW_EINVAL, "unknown precision");
@@ -431,6 +434,7 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
 }
 
 hw_status hw_set_state(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, double t) {
+  hw::NvtxRange nvtx_("hw_set_state");
   if (!s || !Wbar || !Vbar || !Ybar) return fail(HW_EINVAL, "null pointer");
   return upload_state(s, Wbar, Vbar, Ybar, t);
 }
@@ -438,6 +442,7 @@ hw_status hw_set_state(hw_solver* s, const double* Wbar, const double* Vbar, con
 constexpr int64_t kMaxProfiledSteps = 4096;
 
 hw_status hw_step(hw_solver* s, double dt) {
+  hw::NvtxRange nvtx_("hw_step");
   if (!s) return fail(HW_EINVAL, "null solver");
   const StepArgs a = s->args(s->cur, dt > 0 ? dt : 0.0);
   if (s->profiling && s->nprof < kMaxProfiledSteps) {
@@ -479,6 +484,7 @@ static hw_status ensure_graph(hw_solver* s, int parity) {
 }
 
 hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps) {
+  hw::NvtxRange nvtx_("hw_run_to");
   if (!s) return fail(HW_EINVAL, "null solver");
   if (!(T == T)) return fail(HW_EINVAL, "T is NaN");
   HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
@@ -503,6 +509,7 @@ hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps) {
 }
 
 hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, double* t) {
+  hw::NvtxRange nvtx_("hw_get_state");
   if (!s) return fail(HW_EINVAL, "null solver");
   const size_t plane = (size_t)s->m * s->N * sizeof(double);
   double* stage = reinterpret_cast<double*>(s->ws + s->L.stage);
@@ -735,6 +742,7 @@ hw_status hw_pb_bytes(const hw_solver* s, size_t* bytes) {
 }
 
 hw_status hw_step_keep(hw_solver* s, double dt, void* pb_out) {
+  hw::NvtxRange nvtx_("hw_step_keep");
   if (!s || !pb_out) return fail(HW_EINVAL, "null pointer");
   if (reinterpret_cast<uintptr_t>(pb_out) % 16) return fail(HW_EINVAL, "edge-point buffer must be 16-byte aligned");
   StepArgs a = s->args(s->cur, dt > 0 ? dt : 0.0);
@@ -753,6 +761,7 @@ hw_status hw_adjoint_scratch_bytes(const hw_solver* s, size_t* bytes) {
 
 hw_status hw_step_adjoint(hw_solver* s, double dt, const void* U_n, const void* Pb_n, const void* Ubar_next,
                           void* Ubar_n, void* scratch, size_t scratch_bytes) {
+  hw::NvtxRange nvtx_("hw_step_adjoint");
   if (!s || !U_n || !Ubar_next || !Ubar_n || !scratch) return fail(HW_EINVAL, "null pointer");
   if (s->eq != HW_EULER) return fail(HW_EINVAL, "the adjoint step is implemented for the Euler equations");
   if (s->opt.positivity) return fail(HW_EINVAL, "the adjoint step does not cover the scale limiter");

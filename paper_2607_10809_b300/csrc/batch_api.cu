@@ -12,6 +12,7 @@
 
 #include "../../include/hweno.h"
 #include "internal.h"
+#include "nvtx.h"
 #include "kernels.h"
 
 using namespace hw;
@@ -237,6 +238,7 @@ hw_status hw_batch_workspace_bytes(const hw_mesh* const* meshes, int32_t n, cons
 hw_status hw_batch_create(const hw_mesh* const* meshes, int32_t n, const hw_options* opt, int32_t precision,
                           const double* const* Wbar, const double* const* Vbar, const double* const* Ybar,
                           void* workspace, size_t workspace_bytes, void* cuda_stream, hw_batch** out) {
+  hw::NvtxRange nvtx_("hw_batch_create");
   if (hw_status st = check_batch_args(meshes, n, opt, precision)) return st;
   if (!Wbar || !Vbar || !Ybar || !workspace || !out) return bfail(HW_EINVAL, "null pointer");
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return bfail(HW_EINVAL, "workspace must be 256-byte aligned");
@@ -359,6 +361,7 @@ hw_status hw_batch_get_schedule(const hw_batch* b, hw_batch_schedule* s, int32_t
 }
 
 hw_status hw_batch_run_to(hw_batch* b, double T, int64_t* cell_steps) {
+  hw::NvtxRange nvtx_("hw_batch_run_to");
   if (!b) return bfail(HW_EINVAL, "null batch");
   if (!(T == T)) return bfail(HW_EINVAL, "T is NaN");
   launch_batch_dt(b->bs(), b->n, b->opt.cfl, T, 1, b->stream);
@@ -387,6 +390,7 @@ hw_status hw_batch_run_to(hw_batch* b, double T, int64_t* cell_steps) {
 }
 
 hw_status hw_batch_steps(hw_batch* b, int32_t steps, double* ms) {
+  hw::NvtxRange nvtx_("hw_batch_steps");
   if (!b || steps <= 0) return bfail(HW_EINVAL, "bad arguments");
   launch_batch_dt(b->bs(), b->n, b->opt.cfl, 1e300, 1, b->stream);
   if (hw_status st = capture_graph(b, steps)) return st;
@@ -415,6 +419,7 @@ hw_status hw_batch_reset(hw_batch* b) {
 }
 
 hw_status hw_batch_autotune(hw_batch* b, int32_t trial_steps, hw_batch_schedule* best, double* best_ms) {
+  hw::NvtxRange nvtx_("hw_batch_autotune");
   if (!b || trial_steps <= 0) return bfail(HW_EINVAL, "bad arguments");
   const int per_sm = batch_blocks_per_sm(b->prec, b->eq, b->eq == HW_EULER && b->opt.positivity);
   hw_batch_schedule base = b->sched, pick = b->sched;
