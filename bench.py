@@ -70,10 +70,10 @@ TRAFFIC = {
 }
 
 # Floating-point operations per cell and launch (FMA counted as 2), from the
-# executed-instruction counters of one ncu capture of the 499,942-cell vortex
-# (smsp__sass_thread_inst_executed_op_{d,f}{fma,add,mul}_pred_on.sum / cells),
+# executed-instruction counters of one ncu capture of the 499,942-cell vortex in
+# FP64 (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum / cells),
 # valid for the sources hash of TRAFFIC.
-FLOPS = {"recon_fp64": 4382, "edge_fp64": 2932, "recon_fp32": 3986, "edge_fp32": 2609}
+FLOPS = {"recon_fp64": 4382, "edge_fp64": 2908}
 
 # FP64 peak of the B300 per SM clock: the nominal 1.25 TFLOP/s at the 2032 MHz
 # maximum clock is 2 FP64 FMA per SM per clock on 148 SMs (a one-off FMA probe

@@ -18,6 +18,7 @@
 using namespace hw;
 
 namespace {
+constexpr int kCompactChunk = 128;   // steps per launch of a run, at most (tail compaction between launches)
 hw_status bfail(hw_status s, const std::string& msg) {
   hw_set_last_error_internal(msg.c_str());
   return s;
@@ -104,6 +105,8 @@ struct hw_batch {
   hw_batch_schedule sched{};
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  int graph_ntiles = 0;                 // tile count the graph was captured for
+  int cur_ntiles = 0;                   // tiles in the device table (all, or the running solves')
   int sms = 148;
   BatchSolve* h_bs = nullptr;          // pinned mirrors
   BatchCtl* h_ctl = nullptr;
@@ -122,7 +125,7 @@ struct hw_batch {
     a.C = L.comp_bytes ? ws + L.comp : nullptr;
     a.maps = &maps;
     a.tiles = reinterpret_cast<const int4*>(ws + L.tiles);
-    a.ntiles = plan.ntiles;
+    a.ntiles = cur_ntiles > 0 ? cur_ntiles : plan.ntiles;
     a.bs = bs();
     a.ctl = ctl();
     a.nsolves = n;
@@ -132,7 +135,7 @@ struct hw_batch {
     a.withhold_block = sched.withhold_block;
     const int per_sm = batch_blocks_per_sm(prec, eq, eq == HW_EULER && opt.positivity);
     const int bps = std::max(1, std::min(sched.blocks_per_sm > 0 ? sched.blocks_per_sm : per_sm, per_sm));
-    a.grid = std::max(1, std::min(bps * sms, plan.ntiles));
+    a.grid = std::max(1, std::min(bps * sms, a.ntiles));
     a.P.ax = opt.ax; a.P.ay = opt.ay; a.P.gam = opt.gamma_gas; a.P.eps = opt.eps;
     for (int l = 0; l < 4; ++l) { a.P.g[l] = opt.gamma_lin[l]; a.P.win[l] = opt.inflow[l]; }
     eq_params_finish(a.P);
@@ -171,15 +174,27 @@ std::vector<int4> tile_table(const hw_batch* b, int order) {
   return t;
 }
 
-hw_status upload_tiles(hw_batch* b) {
-  const std::vector<int4> t = tile_table(b, b->sched.tile_order);
+hw_status upload_table(hw_batch* b, const std::vector<int4>& t) {
   HB_CUDA(cudaMemcpyAsync(b->ws + b->L.tiles, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
   HB_CUDA(cudaStreamSynchronize(b->stream));
+  b->cur_ntiles = (int)t.size();
   return HW_OK;
 }
 
+hw_status upload_tiles(hw_batch* b) { return upload_table(b, tile_table(b, b->sched.tile_order)); }
+
+// Tail compaction of a run: keep only the tiles of the solves still running
+// (same order), so that the persistent grid and its barriers shrink with them.
+hw_status compact_tiles(hw_batch* b) {
+  std::vector<int4> t;
+  for (const int4& e : tile_table(b, b->sched.tile_order))
+    if (!b->h_bs[e.z].done) t.push_back(e);
+  if (t.empty()) return HW_OK;
+  return upload_table(b, t);
+}
+
 hw_status capture_graph(hw_batch* b, int steps) {
-  if (b->graph && b->graph_steps == steps) return HW_OK;
+  if (b->graph && b->graph_steps == steps && b->graph_ntiles == b->cur_ntiles) return HW_OK;
   if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
   cudaGraph_t g = nullptr;
   HB_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -194,6 +209,7 @@ hw_status capture_graph(hw_batch* b, int steps) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(HW_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
   b->graph_steps = steps;
+  b->graph_ntiles = b->cur_ntiles;
   return HW_OK;
 }
 
@@ -366,19 +382,33 @@ hw_status hw_batch_run_to(hw_batch* b, double T, int64_t* cell_steps) {
   if (!(T == T)) return bfail(HW_EINVAL, "T is NaN");
   launch_batch_dt(b->bs(), b->n, b->opt.cfl, T, 1, b->stream);
   HB_CUDA(cudaGetLastError());
-  if (hw_status st = capture_graph(b, b->sched.steps_per_launch)) return st;
+  // chunks of at most kCompactChunk steps; between chunks, once the running
+  // solves hold at most half of the current tiles, the table shrinks to them
+  const int chunk = std::max(1, std::min(b->sched.steps_per_launch, kCompactChunk));
   if (hw_status st = read_status(b)) return st;
   std::vector<long long> n0(b->n);
   for (int k = 0; k < b->n; ++k) n0[k] = b->h_bs[k].nsteps;
+  hw_status result = HW_OK;
   for (long long iter = 0;; ++iter) {
     bool all_done = true;
-    for (int k = 0; k < b->n; ++k) all_done = all_done && b->h_bs[k].done;
+    int64_t active_tiles = 0;
+    for (int k = 0; k < b->n; ++k) {
+      all_done = all_done && b->h_bs[k].done;
+      if (!b->h_bs[k].done) active_tiles += (b->plan.nt[k] + kCells - 1) / kCells;
+    }
     if (all_done) break;
-    if (iter > (1ll << 24)) return bfail(HW_ESTATE, "batch did not reach T");
+    if (iter > (1ll << 24)) { result = bfail(HW_ESTATE, "batch did not reach T"); break; }
+    if (2 * active_tiles <= b->cur_ntiles)
+      if ((result = compact_tiles(b)) != HW_OK) break;
+    if ((result = capture_graph(b, chunk)) != HW_OK) break;
     HB_CUDA(cudaGraphLaunch(b->graph, b->stream));
-    if (hw_status st = read_status(b)) return st;
-    if (b->h_ctl->flags & 2u) return bfail(HW_ETIMEOUT, "batched kernel: a bounded wait gave up");
+    if ((result = read_status(b)) != HW_OK) break;
+    if (b->h_ctl->flags & 2u) { result = bfail(HW_ETIMEOUT, "batched kernel: a bounded wait gave up"); break; }
   }
+  if (b->cur_ntiles != b->plan.ntiles) {   // the full table again for the next call
+    if (hw_status st = upload_tiles(b)) return st;
+  }
+  if (result != HW_OK) return result;
   if (cell_steps) {
     int64_t cs = 0;
     for (int k = 0; k < b->n; ++k) cs += (b->h_bs[k].nsteps - n0[k]) * b->plan.nt[k];

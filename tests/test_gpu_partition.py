@@ -42,3 +42,25 @@ def test_three_parts_match_one_solver(precision, tol):
     err = (np.abs(U - Ur).max(axis=-1) / np.abs(Ur).max(axis=-1)).max()
     print(f"{precision}: 3 parts vs one solver, {nsteps} steps: relative Linf {err:.2e}")
     assert err < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_three_parts_device_exchange_match_one_solver(precision, tol):
+    """The same with the halo rows moved device to device (internal state
+    buffers, torch indexing): no host round trip."""
+    mesh = I.poisson_delaunay_periodic(10.0, 3000, seed=21)
+    U0 = I.initial_state(mesh, I.vortex, 4)
+    ref = hweno.Solver(mesh, U0, eq="euler", precision=precision)
+    nsteps = 8
+    for _ in range(nsteps):
+        ref.step()
+    Ur, tr = ref.get_state()
+    parts = PT.build(mesh, hweno.Mesh(mesh).permutation(), 3)
+    steppers = [PT.DeviceStepper(hweno.Solver(p.mesh, PT.scatter_state(U0, p), eq="euler", precision=precision), p)
+                for p in parts]
+    t = PT.run_local_device(parts, steppers, nsteps)
+    U = PT.gather_state(parts, [s.get() for s in steppers], mesh.nt)
+    assert abs(t - tr) <= 1e-14 * tr
+    err = (np.abs(U - Ur).max(axis=-1) / np.abs(Ur).max(axis=-1)).max()
+    print(f"{precision}: 3 parts (device exchange) vs one solver, {nsteps} steps: relative Linf {err:.2e}")
+    assert err < tol
