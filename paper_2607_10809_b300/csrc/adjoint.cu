@@ -384,13 +384,16 @@ namespace {
 template <typename R> void launch_adjoint_t(const AdjointArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(AdjTile<R>);
   static_assert(sizeof(AdjTile<R>) <= 227 * 1024, "tile fits the shared memory of one block");
-  int dev = 0, sms = 148, per_sm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaFuncSetAttribute(k_adj_step<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_step<R>, kAdjThreads, smem);
+  static const int cap = [smem] {   // resident blocks (occupancy x SMs), once per process
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_adj_step<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_step<R>, kAdjThreads, smem);
+    return sms * std::max(1, per_sm);
+  }();
   const int ntiles = (a.N + kAdjCells - 1) / kAdjCells;
-  const int grid = std::max(1, std::min(ntiles, sms * std::max(1, per_sm)));
+  const int grid = std::max(1, std::min(ntiles, cap));
   AdjPtrs p{a.rgeo, a.igeo, a.U, a.Pb, a.Ubar_next, a.N, a.ld};
   k_adj_step<R><<<grid, kAdjThreads, smem, st>>>(p, reinterpret_cast<R*>(a.Cb), a.P, a.dt, ntiles);
   GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
