@@ -2,11 +2,15 @@
 times: the 2M-triangle Euler vortex, the 200k-triangle Burgers problem and
 the 256-solve batch, against the FP64 CPU oracle on sampled outputs (cells,
 solves) that the oracle computes one by one, plus properties that hold at any
-size (conservation on periodic meshes, positivity under the scale limiter)."""
+size (conservation on periodic meshes, positivity under the scale limiter).
+Where the oracle can afford it, whole runs: the 200k Burgers problem to its
+final time (oracle steps split over processes) and the smallest batched
+solves to theirs."""
 import numpy as np
 import pytest
 
 import oracle
+import oracle_pool
 from paper_2607_10809_b300 import build as B
 from paper_2607_10809_b300 import hweno
 from paper_2607_10809_b300 import inputs as I
@@ -105,6 +109,80 @@ def test_euler_vortex_2m_conserves_the_totals():
         print(f"{prec}: drift of the totals over 20 steps {drift.max():.2e}")
         assert drift.max() < tol, (prec, drift)
         s.close()
+
+
+def rel_linf(a, b):
+    """max over cells of |a - b| / max over cells of |b|, per (k, c) plane."""
+    num = np.abs(a - b).max(axis=-1)
+    den = np.maximum(np.abs(b).max(axis=-1), 1e-300)
+    return (num / den).max()
+
+
+def test_burgers_200k_fp64_full_run():
+    """C2 at its configured size (199,712 triangles), FP64, the whole run to
+    T = 1.5 / pi^2 (about 295 CFL steps on both sides) against the oracle,
+    whose steps' cells are split over worker processes.  The split changes
+    only the order in which the oracle adds the edge terms of the cells at the
+    split points (1e-14 after 19 steps of a small case)."""
+    mesh = I.config2_mesh()
+    U0 = I.initial_state(mesh, I.burgers_sine, 1)
+    T = 1.5 / np.pi ** 2
+    s = hweno.Solver(mesh, U0, eq="burgers", precision="fp64")
+    n = s.run_to(T)
+    Ug, t = s.get_state()
+    s.close()
+    Uo, dts = oracle_pool.run_to(mesh, "burgers", U0, T)
+    err = rel_linf(Ug, Uo)
+    print(f"Burgers 200k full run: {n} GPU steps, {len(dts)} oracle steps, FP64 relative Linf {err:.2e}")
+    assert n == len(dts) and abs(t - T) < 1e-14
+    assert err < FP64_TOL
+
+
+def test_batch_smallest_solves_fp64_full_run_to_T():
+    """The three smallest of the 256 four-quadrant solves (chosen by size
+    alone: the oracle's cost), FP64 with the scale limiter and flux blending,
+    over their whole runs to the configured T = 0.25.
+
+    Every step is held to the oracle from the oracle's own state (the step
+    map, unique, at 1e-13).  Whole runs are not: the limiter's and the
+    blending's decisions depend discontinuously on their inputs, so two
+    correct runs whose roundings differ drift apart along a shocked
+    trajectory (measured on solve 176: every one-step difference at most
+    1.6e-14, the free-running difference 6e-13 after 80 steps and 1.2e-9
+    after 280).  The batched launch's whole runs are therefore held to the
+    oracle's in a looser norm (relative L1 1e-9, relative L-infinity 1e-6)
+    and must take the same number of steps to T."""
+    meshes, states = I.config4_batch(256)
+    T = 0.25
+    ks = [int(k) for k in np.argsort([m.nt for m in meshes], kind="stable")[:3]]
+    b = hweno.Batch([meshes[k] for k in ks], [states[k] for k in ks], eq="euler", precision="fp64",
+                    positivity=True)
+    b.run_to(T)
+    got = [b.get_state(i) for i in range(len(ks))]
+    b.close()
+    trajs = oracle_pool.trajectories_many([(meshes[k], "euler", states[k], T, {"positivity": True}) for k in ks])
+    for k, (Ug, t, nsteps, failed), (traj, dts) in zip(ks, got, trajs):
+        # the step map along the oracle's trajectory
+        s = hweno.Solver(meshes[k], states[k], eq="euler", precision="fp64", positivity=True)
+        tn, step_err = 0.0, 0.0
+        for n, dt in enumerate(dts):
+            s.set_state(traj[n], tn)
+            s.step(float(dt))
+            step_err = max(step_err, rel_linf(s.get_state()[0], traj[n + 1]))
+            tn += float(dt)
+        s.close()
+        # the batched whole run
+        Uo = traj[-1]
+        assert not failed and abs(t - T) < 1e-14
+        area = I.cell_areas(meshes[k])
+        l1 = float(((np.abs(Ug - Uo) * area).sum(axis=-1) /
+                    np.maximum((np.abs(Uo) * area).sum(axis=-1), 1e-300)).max())
+        err = rel_linf(Ug, Uo)
+        print(f"solve {k} ({meshes[k].nt} triangles) to T = {T}: {len(dts)} steps, largest one-step relative "
+              f"Linf {step_err:.2e}; batched whole run ({nsteps} steps) relative L1 {l1:.2e}, Linf {err:.2e}")
+        assert step_err < 1e-13
+        assert nsteps == len(dts)
+        assert l1 < 1e-9 and err < 1e-6
 
 
 # The batched Riemann solves run FP32 with the scale limiter in the benchmark;
