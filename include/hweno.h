@@ -166,13 +166,14 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
  * until the stream reaches it (pinned memory gives a true asynchronous copy). */
 hw_status hw_set_state(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, double t);
 /* One time step, asynchronous on the stream.  dt > 0: that step size; dt <= 0:
- * the CFL step held on the device (clipped to the target time of the last
- * hw_run_to, if any). */
+ * the CFL step held on the device (a target time of hw_run_to holds only
+ * inside that call). */
 hw_status hw_step(hw_solver* s, double dt);
 /* Advance to time T with CFL steps (last one clipped to hit T) through a
  * captured CUDA graph of several steps; synchronises.  nsteps (may be NULL)
  * receives the number of steps taken.  Returns HW_ENONFINITE if the state went
- * non-finite / non-physical. */
+ * non-finite / non-physical.  On return the target is cleared: later hw_step
+ * calls advance the state again. */
 hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps);
 /* Copy the state back to host arrays in the caller's numbering and report the
  * time; synchronises.  Any pointer may be NULL to skip it.  HW_FP32: Wbar is

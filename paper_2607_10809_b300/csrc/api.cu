@@ -490,7 +490,15 @@ hw_status hw_run_to(hw_solver* s, double T, int64_t* nsteps) {
   HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));
   HW_CUDA(cudaStreamSynchronize(s->stream));
   const long long n0 = s->h_sc->nsteps;
+  // The target holds only inside this call: the captured graph runs several
+  // steps per launch and the steps past T must leave the state as it is.
+  // Afterwards hw_step steps again (with the unclipped CFL step).
+  struct ClearTarget {
+    hw_solver* s;
+    ~ClearTarget() { launch_set_target(s->sc(), 0.0, 0, s->stream); }
+  };
   launch_set_target(s->sc(), T, 1, s->stream);
+  ClearTarget clear_{s};
   if (hw_status st = ensure_graph(s, s->cur)) return st;
   for (long long iter = 0;; ++iter) {
     HW_CUDA(cudaMemcpyAsync(s->h_sc, s->sc(), sizeof(DevScalars), cudaMemcpyDeviceToHost, s->stream));

@@ -87,6 +87,38 @@ def test_euler_vortex_2m_one_step_sampled():
     check("Euler vortex", mesh, cells, one_step_parity(mesh, U0, "euler", cells))
 
 
+def test_euler_vortex_2m_whole_run_sampled_steps():
+    """C3 at its configured size over the whole run to T = 2 (about 7,450
+    CFL steps; the oracle itself would need about two hours on 16 cores): at
+    t = 0.5, 1, 1.5 and 2 of the GPU's own run (reached with run_to), the CFL
+    step of the GPU state and the next step on 4,000 sampled cells (around the
+    moving vortex and at random) are held to the oracle's from that same
+    state, in FP64 at 1e-12 and in FP32 at the one-step tolerances."""
+    mesh = I.config3_mesh()
+    U0 = I.initial_state(mesh, I.vortex, 4)
+    o = oracle.Oracle(mesh, "euler")
+    solvers = {prec: hweno.Solver(mesh, U0, eq="euler", precision=prec) for prec in ("fp64", "fp32")}
+    for k, Tk in enumerate((0.5, 1.0, 1.5, 2.0)):
+        cells = sample_cells(mesh, 3000, ((5.0 + Tk) % 10.0, (5.0 + Tk) % 10.0), 1000, seed=20 + k)
+        err = {}
+        for prec, s in solvers.items():
+            s.run_to(Tk)
+            Uk, t = s.get_state()
+            _, dt, n = s.time()
+            if prec == "fp64":
+                dt_o = o.cfl_dt(Uk)
+                assert abs(dt - dt_o) <= 1e-14 * dt_o, (dt, dt_o)
+            s.step(dt)
+            Ug, _ = s.get_state()
+            Uo = np.zeros_like(Ug)
+            Uo[:, :, cells] = o.step_cells(Uk, dt, cells)
+            scale = np.maximum(np.abs(Ug).max(axis=-1), 1e-300)
+            err[prec] = sampled_rel(Ug, Uo, cells, scale)
+        check(f"Euler vortex at t = {Tk} (step {n})", mesh, cells, err)
+    for s in solvers.values():
+        s.close()
+
+
 def test_burgers_200k_one_step_sampled():
     mesh = I.config2_mesh()
     U0 = I.initial_state(mesh, I.burgers_sine, 1)
@@ -249,7 +281,7 @@ def test_batch_256_solves_fp32_positivity_and_completion():
 
 
 # Full runs at the benchmark sizes: the FP32 form against the FP64 form (the
-# oracle itself cannot run 2M triangles for 3,800 steps; the FP64 GPU state is
+# oracle itself cannot run 2M triangles for 7,450 steps; the FP64 GPU state is
 # held to the oracle by the sampled tests above), both against the exact
 # solution.  Errors of the cell averages W, per component: L1 area weighted.
 @pytest.mark.parametrize("case", ["burgers200k", "vortex2m"])

@@ -48,6 +48,29 @@ def test_advection_config1_fp64_full_run():
     assert rel_linf(Ug, Uo) < FP64_TOL
 
 
+def test_step_after_run_to_advances():
+    """The target of run_to holds only inside that call: afterwards step()
+    takes the CFL step of the state reached (or the given step) and matches
+    the oracle's step from it."""
+    mesh = I.config1_mesh(10)
+    U0 = I.initial_state(mesh, I.advection_sine, 1)
+    o = oracle.Oracle(mesh, "advection")
+    s = hweno.Solver(mesh, U0, eq="advection", precision="fp64")
+    s.run_to(0.1)
+    U1, t1 = s.get_state()
+    _, dt, _ = s.time()
+    assert abs(t1 - 0.1) < 1e-15 and abs(dt - o.cfl_dt(U1)) <= 1e-14 * dt
+    s.step()
+    U2, t2 = s.get_state()
+    assert abs(t2 - (t1 + dt)) < 1e-15
+    assert rel_linf(U2, o.step(U1, dt)) < FP64_TOL
+    s.step(0.5 * dt)
+    U3, t3 = s.get_state()
+    assert abs(t3 - (t2 + 0.5 * dt)) < 1e-15
+    assert rel_linf(U3, o.step(U2, 0.5 * dt)) < FP64_TOL
+    s.close()
+
+
 @pytest.mark.parametrize("T", [1.5 / np.pi ** 2, 1.5 / np.pi])
 def test_burgers_jittered_fp64_smooth_and_shocked(T):
     mesh = I.jittered_periodic(24, 4.0, 0.15, seed=2)
