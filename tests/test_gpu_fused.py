@@ -114,7 +114,11 @@ def test_default_is_the_two_kernel_step():
         assert hweno.Solver(mesh, U0, eq="euler", precision=prec).step_kernels() == "separate"
 
 
-def test_fused_conservation_and_reached_target_keeps_state():
+def test_fused_conservation_and_steps_past_the_target():
+    """run_to replays a graph of several steps per launch; the steps past the
+    target keep the state (the kernel's branch for a reached target), so the
+    fused run lands on T bitwise equal to the two-kernel run.  After run_to,
+    step() advances again."""
     mesh = I.poisson_delaunay_periodic(10.0, 2_000, seed=9)
     U0 = I.initial_state(mesh, I.vortex, 4)
     s = hweno.Solver(mesh, U0, eq="euler", precision="fp64", step_kernels="fused")
@@ -122,6 +126,12 @@ def test_fused_conservation_and_reached_target_keeps_state():
     s.run_to(0.2)
     np.testing.assert_allclose(s.conservation(), c0, rtol=1e-14)
     U1, t1 = s.get_state()
-    s.step()   # the target is reached: the state is kept
+    r = hweno.Solver(mesh, U0, eq="euler", precision="fp64", step_kernels="separate")
+    r.run_to(0.2)
+    Ur, tr = r.get_state()
+    r.close()
+    assert abs(t1 - 0.2) < 1e-15 and tr == t1 and np.array_equal(U1, Ur)
+    s.step()
     U2, t2 = s.get_state()
-    assert t2 == t1 and np.array_equal(U1, U2)
+    assert t2 > t1 and not np.array_equal(U1, U2)
+    s.close()
