@@ -224,18 +224,22 @@ hw_status hw_step_static_scratch(hw_solver* s, double dt);
 /* ---------------------------------------------------------------------------
  * Device-side state buffers and the adjoint of a step.
  * An internal state buffer holds the state of every cell in the library's
- * internal order and precision: hw_state_bytes() bytes, caller-allocated
- * device memory, 16-byte aligned. */
+ * internal order and precision: the records [ld][3m] (ld = ntri rounded up to
+ * a multiple of 32; per cell Wbar, Vbar, Ybar, m values each), then, in
+ * HW_FP32, the compensation words [ld][m] of the averages (the rounding error
+ * the compensated update carries into the next step).  hw_state_bytes()
+ * bytes, caller-allocated device memory, 16-byte aligned. */
 hw_status hw_state_bytes(const hw_solver* s, size_t* bytes);
 /* Copy the current state to / from an internal buffer (device to device,
- * asynchronous on the stream).  Import also sets the time to t and recomputes
- * the CFL step.  The FP32 compensation words are not part of the buffer:
- * import (like hw_set_state) starts them at zero. */
+ * asynchronous on the stream), compensation words included, so that an
+ * export / import round trip continues the run bit for bit.  Import also sets
+ * the time to t and recomputes the CFL step. */
 hw_status hw_state_export(hw_solver* s, void* dst);
 hw_status hw_state_import(hw_solver* s, const void* src, double t);
 /* Convert host arrays (caller numbering, double, as for hw_get_state) to an
  * internal buffer and back; pure permutation and precision conversion (used
- * for cotangents); synchronise. */
+ * for cotangents); synchronise.  To a buffer: its compensation words are set to
+ * zero.  From a buffer: the records alone (as for a cotangent). */
 hw_status hw_host_to_internal(hw_solver* s, const double* Wbar, const double* Vbar, const double* Ybar, void* dst);
 hw_status hw_internal_to_host(hw_solver* s, const void* src, double* Wbar, double* Vbar, double* Ybar);
 /* Edge-point buffer: the time-Taylor data (W, W_t, W_tt) of every cell at

@@ -674,7 +674,10 @@ extern "C" hw_status hw_step_static_scratch(hw_solver* s, double dt) {
 // ---------------------------------------------------------------------------
 // State buffers on the device, and the adjoint of a step.
 namespace {
-size_t state_bytes(const hw_solver* s) { return (size_t)3 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4); }
+// Internal state buffer: the records [ld][3m] in the solver's precision, then
+// (FP32) the compensation words [ld][m] of the averages.
+size_t state_record_bytes(const hw_solver* s) { return (size_t)3 * s->m * s->ld * (s->prec == HW_FP64 ? 8 : 4); }
+size_t state_bytes(const hw_solver* s) { return state_record_bytes(s) + s->L.comp_bytes; }
 
 struct AdjointScratch {
   size_t Cb, sc, total;
@@ -701,14 +704,21 @@ hw_status hw_state_bytes(const hw_solver* s, size_t* bytes) {
 
 hw_status hw_state_export(hw_solver* s, void* dst) {
   if (!s || !dst) return fail(HW_EINVAL, "null pointer");
-  HW_CUDA(cudaMemcpyAsync(dst, s->U(s->cur), state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+  const size_t rb = state_record_bytes(s);
+  HW_CUDA(cudaMemcpyAsync(dst, s->U(s->cur), rb, cudaMemcpyDeviceToDevice, s->stream));
+  if (s->L.comp_bytes)
+    HW_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + rb, s->comp(), s->L.comp_bytes, cudaMemcpyDeviceToDevice,
+                            s->stream));
   return HW_OK;
 }
 
 hw_status hw_state_import(hw_solver* s, const void* src, double t) {
   if (!s || !src) return fail(HW_EINVAL, "null pointer");
-  HW_CUDA(cudaMemcpyAsync(s->U(s->cur), src, state_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
-  if (hw_status st = s->clear_comp()) return st;
+  const size_t rb = state_record_bytes(s);
+  HW_CUDA(cudaMemcpyAsync(s->U(s->cur), src, rb, cudaMemcpyDeviceToDevice, s->stream));
+  if (s->L.comp_bytes)
+    HW_CUDA(cudaMemcpyAsync(s->comp(), static_cast<const char*>(src) + rb, s->L.comp_bytes,
+                            cudaMemcpyDeviceToDevice, s->stream));
   launch_reset(s->sc(), t, s->opt.cfl, s->stream);
   launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
   HW_CUDA(cudaGetLastError());
@@ -724,6 +734,8 @@ hw_status hw_host_to_internal(hw_solver* s, const double* Wbar, const double* Vb
   HW_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(stage) + 2 * plane, Ybar, plane, cudaMemcpyHostToDevice, s->stream));
   launch_scatter(s->prec, stage, reinterpret_cast<const int32_t*>(s->ws + s->L.perm), (int)s->N, (int)s->ld,
                  3 * s->m, dst, s->stream);
+  if (s->L.comp_bytes)   // a state given as plain values: no compensation
+    HW_CUDA(cudaMemsetAsync(static_cast<char*>(dst) + state_record_bytes(s), 0, s->L.comp_bytes, s->stream));
   HW_CUDA(cudaGetLastError());
   HW_CUDA(cudaStreamSynchronize(s->stream));
   return HW_OK;

@@ -221,9 +221,11 @@ class SolverStepper:
 class DeviceStepper:
     """A part's solver with its halo exchange in device memory: the state is
     exported to an internal state buffer (the library's per-cell records, in
-    its internal order), the exchanged rows are read and written there, and
-    the buffer is imported back (which also recomputes the CFL step).  In FP32
-    the import starts the compensation words of the averages at zero."""
+    its internal order, then in FP32 the compensation words of the averages),
+    the exchanged rows are read and written there, and the buffer is imported
+    back (which also recomputes the CFL step).  A row sent to another part
+    carries the cell's record and, in FP32, its compensation words, so the
+    partitioned run is the single run bit for bit."""
 
     def __init__(self, solver, part: Part):
         import torch
@@ -233,10 +235,16 @@ class DeviceStepper:
         inv = np.empty_like(perm)
         inv[perm] = np.arange(perm.size)
         self.buf = solver.state_buffer()
-        dtype = torch.float32 if solver.precision == "fp32" else torch.float64
+        fp32 = solver.precision == "fp32"
+        dtype = torch.float32 if fp32 else torch.float64
         m = solver.m
-        nrec = self.buf.numel() // (3 * m * (4 if dtype == torch.float32 else 8))
-        self.rows = self.buf.view(dtype).view(nrec, 3 * m)
+        words = 4 * m if fp32 else 3 * m            # words per cell in the buffer
+        nrec = self.buf.numel() // (words * (4 if fp32 else 8))
+        flat = self.buf.view(dtype)
+        self.rec = flat[: nrec * 3 * m].view(nrec, 3 * m)
+        self.comp = flat[nrec * 3 * m: nrec * 4 * m].view(nrec, m) if fp32 else None
+        self.width = words
+        self.dtype = dtype
         dev = self.buf.device
         self.send_rows = {q: torch.from_numpy(inv[idx].astype(np.int64)).to(dev) for q, idx in part.send.items()}
         self.recv_rows = {q: torch.from_numpy(inv[idx].astype(np.int64)).to(dev) for q, idx in part.recv.items()}
@@ -251,10 +259,17 @@ class DeviceStepper:
         self.s.export_state(self.buf)
 
     def outgoing(self, q):
-        return self.rows.index_select(0, self.send_rows[q])
+        import torch
+        idx = self.send_rows[q]
+        r = self.rec.index_select(0, idx)
+        return r if self.comp is None else torch.cat([r, self.comp.index_select(0, idx)], dim=1)
 
     def incoming(self, q, data) -> None:
-        self.rows.index_copy_(0, self.recv_rows[q], data)
+        idx = self.recv_rows[q]
+        m3 = self.rec.shape[1]
+        self.rec.index_copy_(0, idx, data[:, :m3].contiguous())
+        if self.comp is not None:
+            self.comp.index_copy_(0, idx, data[:, m3:].contiguous())
 
     def commit(self, t: float) -> None:
         self.s.import_state(self.buf, t)
@@ -298,8 +313,7 @@ def run_distributed_device(part: Part, stepper: "DeviceStepper", nsteps: int, t0
         for q in sorted(part.send):
             reqs.append(dist.isend(stepper.outgoing(q), dst=q))
         for q in sorted(part.recv):
-            inbox[q] = torch.empty((stepper.recv_rows[q].numel(), stepper.rows.shape[1]), dtype=stepper.rows.dtype,
-                                   device=dev)
+            inbox[q] = torch.empty((stepper.recv_rows[q].numel(), stepper.width), dtype=stepper.dtype, device=dev)
             reqs.append(dist.irecv(inbox[q], src=q))
         for r in reqs:
             r.wait()

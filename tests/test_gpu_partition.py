@@ -44,10 +44,12 @@ def test_three_parts_match_one_solver(precision, tol):
     assert err < tol
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
-def test_three_parts_device_exchange_match_one_solver(precision, tol):
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_three_parts_device_exchange_match_one_solver(precision):
     """The same with the halo rows moved device to device (internal state
-    buffers, torch indexing): no host round trip."""
+    buffers, torch indexing): no host round trip.  A row carries the cell's
+    record and, in FP32, its compensation words, so the partitioned run is the
+    single run bit for bit in both precisions."""
     mesh = I.poisson_delaunay_periodic(10.0, 3000, seed=21)
     U0 = I.initial_state(mesh, I.vortex, 4)
     ref = hweno.Solver(mesh, U0, eq="euler", precision=precision)
@@ -63,4 +65,4 @@ def test_three_parts_device_exchange_match_one_solver(precision, tol):
     assert abs(t - tr) <= 1e-14 * tr
     err = (np.abs(U - Ur).max(axis=-1) / np.abs(Ur).max(axis=-1)).max()
     print(f"{precision}: 3 parts (device exchange) vs one solver, {nsteps} steps: relative Linf {err:.2e}")
-    assert err < tol
+    assert np.array_equal(U, Ur)
