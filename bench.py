@@ -268,8 +268,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     B.build()
     hweno.load()
-    if args.only in ("adjoint", "batched"):   # one leg alone (profiling runs)
-        leg = adjoint_leg(args) if args.only == "adjoint" else batched_leg(args, world)
+    if args.only in ("adjoint", "batched", "partition"):   # one leg alone (profiling runs)
+        leg = {"adjoint": adjoint_leg, "batched": lambda a: batched_leg(a, world),
+               "partition": partition_leg}[args.only](args)
         if rank == 0:
             print(json.dumps({"partial_run": True, args.only: leg}), flush=True)
         return
@@ -457,6 +458,8 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = batched if batched is not None else batched_leg(args, world)
     if not args.no_adjoint:
         line["adjoint"] = adjoint_leg(args)
+    if args.partition:
+        line["partition"] = partition_leg(args)
     if not args.no_cpu:
         r = cpu_oracle_rates(mesh, U0, args.cpu_seconds)
         line["cpu_baseline"] = {
@@ -682,6 +685,51 @@ def adjoint_leg(args):
             "grad_fp32_vs_fp64_rel_linf": err}
 
 
+# ---------------------------------------------------------------- partition leg
+def partition_leg(args):
+    """One mesh cut into P parts (Hilbert ranges + two halo rings), the parts
+    advanced one after another on this one GPU with the device-resident halo
+    exchange: the partitioned step's cost on one GPU, split into the parts'
+    step kernels (CUDA events) and the rest (dt minimum over the parts, halo
+    rows out and in, CFL refresh, host calls).  On P GPUs the parts' steps would run side by side; this measures
+    the redundant halo work and the exchange's device-side cost, not a
+    scaling curve."""
+    import torch
+    from paper_2607_10809_b300 import hweno
+    from paper_2607_10809_b300 import partition as PT
+    mesh, U0 = workload(args.workload)
+    N = mesh.nt
+    perm = hweno.Mesh(mesh).permutation()
+    out = {"workload": f"{args.workload}: {N} triangles, FP32", "parts": {}}
+    K = args.partition_steps
+    for P in [int(x) for x in (args.partition or "2,4").split(",")]:
+        parts = PT.build(mesh, perm, P)
+        steppers = [PT.DeviceStepper(hweno.Solver(p.mesh, PT.scatter_state(U0, p), eq="euler", precision="fp32"), p)
+                    for p in parts]
+        PT.run_local_device(parts, steppers, 3)
+        torch.cuda.synchronize()
+        for st in steppers:
+            st.s.profile(True)      # the parts' step kernels, timed with CUDA events
+        t0 = time.perf_counter()
+        PT.run_local_device(parts, steppers, K)
+        torch.cuda.synchronize()
+        total = (time.perf_counter() - t0) / K
+        steps_only = 0.0
+        for st in steppers:
+            pr = st.s.profile_read()
+            st.s.profile(False)
+            steps_only += (pr["recon_ms"] + pr["edge_ms"]) * 1e-3 / pr["steps"]
+        local = int(sum(p.cells.size for p in parts))
+        out["parts"][str(P)] = {"ms_per_step": total * 1e3, "parts_steps_ms": steps_only * 1e3,
+                                "exchange_ms": (total - steps_only) * 1e3, "local_cells": local,
+                                "halo_fraction": local / N - 1.0, "steps": K}
+        for st in steppers:
+            st.s.close()
+        del steppers
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The FP64 CPU oracle as the reference arm, on one host core: each step is
@@ -721,7 +769,9 @@ def main():
     ap.add_argument("--batch-T", type=float, default=0.25, help="final time of the batched solves")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) leg")
     ap.add_argument("--adj-steps", type=int, default=200)
-    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "adjoint", "batched"],
+    ap.add_argument("--partition", default="", help="comma-separated part counts of the partition leg (off if empty)")
+    ap.add_argument("--partition-steps", type=int, default=50)
+    ap.add_argument("--only", default="both", choices=["both", "fp32", "fp64", "adjoint", "batched", "partition"],
                     help="precisions to run, or one leg alone")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--acc-steps", type=int, default=50, help="fixed steps of the FP32-vs-FP64 accuracy check")

@@ -183,7 +183,9 @@ hw_status hw_get_state(hw_solver* s, double* Wbar, double* Vbar, double* Ybar, d
  * device in a fixed order (deterministic); sums[c], synchronises. */
 hw_status hw_conservation(hw_solver* s, double* sums);
 /* Device flags latched since the last call (bit 0: non-finite / non-physical
- * state, bit 1: spin limit reached); clears them; synchronises. */
+ * state, bit 1: spin limit reached, bit 2: a row index of
+ * hw_state_rows_export / hw_state_rows_import outside [0, ntri), skipped);
+ * clears them; synchronises. */
 hw_status hw_status_flags(hw_solver* s, uint32_t* flags);
 /* Current time, current device time step and steps taken; synchronises. */
 hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps);
@@ -236,6 +238,18 @@ hw_status hw_state_bytes(const hw_solver* s, size_t* bytes);
  * the time to t and recomputes the CFL step. */
 hw_status hw_state_export(hw_solver* s, void* dst);
 hw_status hw_state_import(hw_solver* s, const void* src, double t);
+/* Rows of the current state, for a halo exchange that moves only the cells
+ * another part of a partitioned mesh holds.  A row is a cell's record (3m
+ * values) followed, in HW_FP32, by its m compensation words, in the solver's
+ * precision: hw_state_row_words() values.  rows: n internal cell indices
+ * (device memory, int32; hw_mesh_permutation maps them to the caller's
+ * numbering); buf: n rows, packed (device memory).  Asynchronous on the
+ * stream.  An index outside [0, ntri) is skipped and raises bit 2 of
+ * hw_status_flags.  Import with refresh != 0 then recomputes the CFL step of
+ * the state (call it with the last batch of rows of a step). */
+hw_status hw_state_row_words(const hw_solver* s, int32_t* words);
+hw_status hw_state_rows_export(hw_solver* s, const int32_t* rows, int64_t n, void* buf);
+hw_status hw_state_rows_import(hw_solver* s, const int32_t* rows, int64_t n, const void* buf, int32_t refresh);
 /* Convert host arrays (caller numbering, double, as for hw_get_state) to an
  * internal buffer and back; pure permutation and precision conversion (used
  * for cotangents); synchronise.  To a buffer: its compensation words are set to

@@ -14,6 +14,7 @@
 #include "../../include/hweno.h"
 #include "internal.h"
 #include "nvtx.h"
+#include "state_rows.h"
 #include "kernels.h"
 
 using namespace hw;
@@ -721,6 +722,29 @@ hw_status hw_state_import(hw_solver* s, const void* src, double t) {
                             cudaMemcpyDeviceToDevice, s->stream));
   launch_reset(s->sc(), t, s->opt.cfl, s->stream);
   launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
+  HW_CUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+hw_status hw_state_row_words(const hw_solver* s, int32_t* words) {
+  if (!s || !words) return fail(HW_EINVAL, "null pointer");
+  *words = (s->L.comp_bytes ? 4 : 3) * s->m;
+  return HW_OK;
+}
+
+hw_status hw_state_rows_export(hw_solver* s, const int32_t* rows, int64_t n, void* buf) {
+  hw::NvtxRange nvtx_("hw_state_rows_export");
+  if (!s || n < 0 || (n > 0 && (!rows || !buf))) return fail(HW_EINVAL, "null pointer or negative count");
+  launch_rows_gather(s->prec, s->U(s->cur), s->comp(), s->m, (int)s->N, rows, n, buf, &s->sc()->flags, s->stream);
+  HW_CUDA(cudaGetLastError());
+  return HW_OK;
+}
+
+hw_status hw_state_rows_import(hw_solver* s, const int32_t* rows, int64_t n, const void* buf, int32_t refresh) {
+  hw::NvtxRange nvtx_("hw_state_rows_import");
+  if (!s || n < 0 || (n > 0 && (!rows || !buf))) return fail(HW_EINVAL, "null pointer or negative count");
+  launch_rows_scatter(s->prec, s->U(s->cur), s->comp(), s->m, (int)s->N, rows, n, buf, &s->sc()->flags, s->stream);
+  if (refresh) launch_cfl(s->prec, s->eq, s->args(s->cur, 0.0), s->stream);
   HW_CUDA(cudaGetLastError());
   return HW_OK;
 }

@@ -28,7 +28,8 @@ EXPORTED = ["hw_options_default", "hw_mesh_create", "hw_mesh_set_boundary", "hw_
             "hw_solver_destroy", "hw_step_kernels", "hw_last_error", "hw_step_static_scratch", "hw_batch_schedule_default",
             "hw_batch_workspace_bytes", "hw_batch_create", "hw_batch_set_schedule", "hw_batch_get_schedule",
             "hw_batch_autotune", "hw_batch_run_to", "hw_batch_steps", "hw_batch_reset", "hw_batch_get_state",
-            "hw_batch_destroy", "hw_state_bytes", "hw_state_export", "hw_state_import", "hw_host_to_internal",
+            "hw_batch_destroy", "hw_state_bytes", "hw_state_export", "hw_state_import", "hw_state_row_words",
+            "hw_state_rows_export", "hw_state_rows_import", "hw_host_to_internal",
             "hw_internal_to_host", "hw_pb_bytes", "hw_step_keep", "hw_adjoint_scratch_bytes", "hw_step_adjoint"]
 
 
@@ -104,6 +105,9 @@ def load():
         "hw_state_bytes": (ctypes.c_int, [vp, P(sz)]),
         "hw_state_export": (ctypes.c_int, [vp, vp]),
         "hw_state_import": (ctypes.c_int, [vp, vp, d]),
+        "hw_state_row_words": (ctypes.c_int, [vp, P(i32)]),
+        "hw_state_rows_export": (ctypes.c_int, [vp, vp, i64, vp]),
+        "hw_state_rows_import": (ctypes.c_int, [vp, vp, i64, vp, i32]),
         "hw_host_to_internal": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "hw_internal_to_host": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "hw_adjoint_scratch_bytes": (ctypes.c_int, [vp, P(sz)]),
@@ -279,6 +283,27 @@ class Solver:
 
     def import_state(self, buf, t=0.0):
         _check(load().hw_state_import(self.h, ctypes.c_void_p(buf.data_ptr()), float(t)))
+
+    def state_row_words(self):
+        """Values per row of hw_state_rows_export / import (record, then in
+        FP32 the compensation words)."""
+        w = ctypes.c_int32()
+        _check(load().hw_state_row_words(self.h, ctypes.byref(w)))
+        return w.value
+
+    def state_rows_export(self, rows, out):
+        """out[k] = row rows[k] of the current state (rows: int32 CUDA tensor of
+        internal cell indices; out: CUDA tensor [len(rows), state_row_words()]
+        of the solver's precision)."""
+        _check(load().hw_state_rows_export(self.h, ctypes.c_void_p(rows.data_ptr()), rows.numel(),
+                                           ctypes.c_void_p(out.data_ptr())))
+
+    def state_rows_import(self, rows=None, buf=None, refresh=False):
+        """Row rows[k] of the current state = buf[k]; refresh: then recompute
+        the CFL step (rows may be None for a refresh alone)."""
+        n = 0 if rows is None else rows.numel()
+        _check(load().hw_state_rows_import(self.h, ctypes.c_void_p(rows.data_ptr() if n else None), n,
+                                           ctypes.c_void_p(buf.data_ptr() if n else None), int(bool(refresh))))
 
     def host_to_internal(self, U, buf):
         U = np.ascontiguousarray(U, dtype=np.float64)

@@ -219,13 +219,13 @@ class SolverStepper:
 
 
 class DeviceStepper:
-    """A part's solver with its halo exchange in device memory: the state is
-    exported to an internal state buffer (the library's per-cell records, in
-    its internal order, then in FP32 the compensation words of the averages),
-    the exchanged rows are read and written there, and the buffer is imported
-    back (which also recomputes the CFL step).  A row sent to another part
-    carries the cell's record and, in FP32, its compensation words, so the
-    partitioned run is the single run bit for bit."""
+    """A part's solver with its halo exchange in device memory: after a step
+    the rows of the cells another part holds are gathered from the state
+    (hw_state_rows_export: the cell's record and, in FP32, its compensation
+    words), the rows of the halo cells are written back into the state
+    (hw_state_rows_import), and the CFL step is recomputed from the updated
+    state.  Only halo rows move, so the partitioned run is the single run bit
+    for bit at a cost set by the halo, not by the part."""
 
     def __init__(self, solver, part: Part):
         import torch
@@ -234,20 +234,11 @@ class DeviceStepper:
         perm = solver.mesh.permutation()           # perm[k] = local index of internal cell k
         inv = np.empty_like(perm)
         inv[perm] = np.arange(perm.size)
-        self.buf = solver.state_buffer()
-        fp32 = solver.precision == "fp32"
-        dtype = torch.float32 if fp32 else torch.float64
-        m = solver.m
-        words = 4 * m if fp32 else 3 * m            # words per cell in the buffer
-        nrec = self.buf.numel() // (words * (4 if fp32 else 8))
-        flat = self.buf.view(dtype)
-        self.rec = flat[: nrec * 3 * m].view(nrec, 3 * m)
-        self.comp = flat[nrec * 3 * m: nrec * 4 * m].view(nrec, m) if fp32 else None
-        self.width = words
-        self.dtype = dtype
-        dev = self.buf.device
-        self.send_rows = {q: torch.from_numpy(inv[idx].astype(np.int64)).to(dev) for q, idx in part.send.items()}
-        self.recv_rows = {q: torch.from_numpy(inv[idx].astype(np.int64)).to(dev) for q, idx in part.recv.items()}
+        self.dtype = torch.float32 if solver.precision == "fp32" else torch.float64
+        self.width = solver.state_row_words()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.send_rows = {q: torch.from_numpy(inv[idx].astype(np.int32)).to(self.device) for q, idx in part.send.items()}
+        self.recv_rows = {q: torch.from_numpy(inv[idx].astype(np.int32)).to(self.device) for q, idx in part.recv.items()}
 
     def cfl_dt(self) -> float:
         return self.s.time()[1]
@@ -256,23 +247,22 @@ class DeviceStepper:
         self.s.step(dt)
 
     def export(self) -> None:
-        self.s.export_state(self.buf)
+        """Nothing to do: outgoing() reads the rows straight from the state."""
 
     def outgoing(self, q):
         import torch
-        idx = self.send_rows[q]
-        r = self.rec.index_select(0, idx)
-        return r if self.comp is None else torch.cat([r, self.comp.index_select(0, idx)], dim=1)
+        rows = self.send_rows[q]
+        out = torch.empty((rows.numel(), self.width), dtype=self.dtype, device=self.device)
+        self.s.state_rows_export(rows, out)
+        return out
 
     def incoming(self, q, data) -> None:
-        idx = self.recv_rows[q]
-        m3 = self.rec.shape[1]
-        self.rec.index_copy_(0, idx, data[:, :m3].contiguous())
-        if self.comp is not None:
-            self.comp.index_copy_(0, idx, data[:, m3:].contiguous())
+        self.s.state_rows_import(self.recv_rows[q], data.contiguous())
 
     def commit(self, t: float) -> None:
-        self.s.import_state(self.buf, t)
+        """The halo rows are in: recompute the CFL step (the time advanced with
+        the step on the device)."""
+        self.s.state_rows_import(refresh=True)
 
     def get(self) -> np.ndarray:
         return self.s.get_state()[0]
@@ -301,7 +291,7 @@ def run_distributed_device(part: Part, stepper: "DeviceStepper", nsteps: int, t0
     import torch
     import torch.distributed as dist
     t = t0
-    dev = stepper.buf.device
+    dev = stepper.device
     for _ in range(nsteps):
         dt = torch.tensor([stepper.cfl_dt()], dtype=torch.float64, device=dev)
         dist.all_reduce(dt, op=dist.ReduceOp.MIN)
