@@ -19,8 +19,9 @@
  *     numbering: Wbar[c*ntri + i] is the average of component c of W over
  *     triangle i, Vbar / Ybar the averages of W_x / W_y (Eq. aver).
  *     Components: 1 for advection and Burgers, 4 (rho, rho u, rho v, E) for Euler.
- *   - The library renumbers cells internally along a Hilbert curve; this never
- *     shows through the interface.
+ *   - The library renumbers cells internally along a Hilbert curve.  Host
+ *     arrays never see it; the device-side state buffers and row calls below
+ *     use the internal numbering (hw_mesh_permutation maps it to the caller's).
  *   - Device memory is owned by the caller: hw_state_init receives a workspace
  *     pointer of at least hw_workspace_bytes() bytes (for instance a torch
  *     uint8 CUDA tensor) and the library never frees it.  The library allocates
