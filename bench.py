@@ -448,7 +448,9 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": (1 if fused else 2) * K,
         "clocks": r32["clocks"],
         "fp64": {"value": replicas_value(N, r64["K"], r64["ms"], world), "steps": r64["K"],
-                 "ms_per_step": r64["ms"] / r64["K"], "kernel_ms": {"k_recon": rec64, "k_edge": edge64},
+                 "ms_per_step": r64["ms"] / r64["K"], "step_kernels": r64["kernels"],
+                 "kernel_ms": {"k_recon": rec64,
+                               ("k_edge_flux+k_edge_update" if r64["kernels"] == "edge_once" else "k_edge"): edge64},
                  "clocks": r64["clocks"], "roofline": fp64_roofline(N, rec64, edge64, r64["clocks"], sha)},
         "status_flags": {"fp32": r32["flags"], "fp64": r64["flags"]},
         "fp32_vs_fp64": acc,
@@ -780,8 +782,8 @@ def main():
     ap.add_argument("--batch-fp64-solves", type=int, default=16,
                     help="solves of the batch re-run one by one in FP64 (accuracy and FP64 throughput)")
     ap.add_argument("--ref-cells", type=int, default=2000)
-    ap.add_argument("--step-kernels", default="default", choices=["default", "separate", "fused"],
-                    help="kernels of the single-solve step (default: fused in FP32, separate in FP64)")
+    ap.add_argument("--step-kernels", default="default", choices=["default", "separate", "fused", "edge_once"],
+                    help="kernels of the single-solve step (default: the two-sided flux kernel in FP32, the edge-once flux phase in FP64)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -89,13 +89,18 @@ typedef struct {
                            evaluation at t_{n+1}.  1 is for the single-solve step only: it
                            is refused with the scale limiter, by the batched form and by
                            the adjoint step (HW_EINVAL) */
-  int32_t step_kernels; /* kernels of a single-solve step: 0 = default = 1, a
-                           reconstruction kernel then a flux kernel with the edge-point
-                           data in the workspace; 2 = one fused reconstruct-and-flux
+  int32_t step_kernels; /* kernels of a single-solve step: 0 = default (3 in HW_FP64,
+                           1 in HW_FP32); 1 = a reconstruction kernel then a flux kernel
+                           with the edge-point data in the workspace, each cell evaluating
+                           the fluxes of its own edges; 2 = one fused reconstruct-and-flux
                            kernel that keeps the edge-point data in shared memory and
                            reconstructs each tile's halo itself (hw_state_init fails with
                            HW_EINVAL if a tile of the mesh has more halo cells than the
-                           kernel holds).  Results agree to rounding. */
+                           kernel holds); 3 = the reconstruction kernel, then the flux
+                           phase with each edge evaluated once (by its left cell) into a
+                           per-point flux buffer of the workspace, then the update kernel
+                           (half the flux arithmetic; meshes below 2^29 cells).  Results
+                           agree bit for bit between 1 and 3, to rounding with 2. */
   double ax, ay;        /* advection velocity (HW_ADVECTION) */
   double gamma_gas;     /* ratio of specific heats (HW_EULER) */
   double cfl;           /* dt = cfl * min_K inradius_K / lambda_K */
@@ -196,9 +201,11 @@ hw_status hw_time(hw_solver* s, double* t, double* dt, int64_t* nsteps);
 hw_status hw_profile(hw_solver* s, int32_t enable);
 /* Synchronises on the recorded events; ms[0] = total reconstruction-kernel
  * time (the fused kernel's, when steps run it), ms[1] = total flux/update-kernel
- * time (0 with the fused kernel), milliseconds over nsteps profiled steps. */
+ * time (both kernels of the edge-once phase; 0 with the fused kernel),
+ * milliseconds over nsteps profiled steps. */
 hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps);
-/* Kernels the solver's steps run: *path = 2 (fused) or 1 (separate). */
+/* Kernels the solver's steps run: *path = 1 (separate), 2 (fused) or 3
+ * (separate, each edge's flux once). */
 hw_status hw_step_kernels(const hw_solver* s, int32_t* path);
 hw_status hw_solver_destroy(hw_solver* s);
 

@@ -38,14 +38,23 @@ constexpr int kGraphSteps = 16;  // steps per captured graph (even: the state pa
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t rgeo, igeo, U0, U1, Pb, comp, comp_bytes, area, perm, stage, sc, partial, consv, fslot, fhoff, fhalo, total;
+  size_t rgeo, igeo, U0, U1, Pb, comp, comp_bytes, area, perm, stage, sc, partial, consv, fslot, fhoff, fhalo;
+  size_t oedges, EP, EP_bytes, total;
 };
 
 // Tile shape of the fused step in a precision.
 int fused_tile(int prec) { return prec == HW_FP32 ? kFusedTile32 : kFusedTile64; }
 int fused_halo_cap(int prec) { return prec == HW_FP32 ? kFusedHalo32 : kFusedHalo64; }
 
-Layout make_layout(int64_t N, int m, int prec) {
+// The flux phase evaluates each edge once (step_kernels 3, and the default
+// in FP64, where the FP64 pipe bounds the step and the halved flux arithmetic
+// pays; in FP32 the two-sided k_edge is faster): edge list and per-point flux
+// buffer in the workspace.
+bool edge_once_mode(const hw_options* o, int prec) {
+  return o->step_kernels == 3 || (o->step_kernels == 0 && prec == HW_FP64);
+}
+
+Layout make_layout(int64_t N, int m, int prec, bool edge_once) {
   const size_t s = prec == HW_FP64 ? 8 : 4;
   const size_t ld = (size_t)padded_cells(N);   // plane stride
   Layout L{};
@@ -70,6 +79,10 @@ Layout make_layout(int64_t N, int m, int prec) {
   L.fslot = take(ld * 4);
   L.fhoff = take((ntiles + 1) * 4);
   L.fhalo = take(ntiles * (size_t)fused_halo_cap(prec) * 4);
+  // edge-once flux phase: owned edges (at most 3 per cell) and [ld][6][2m] values
+  L.oedges = take(edge_once ? (size_t)3 * N * 4 : 0);
+  L.EP_bytes = edge_once ? (size_t)12 * m * ld * s : 0;
+  L.EP = take(L.EP_bytes);
   L.total = o;
   return L;
 }
@@ -133,7 +146,7 @@ hw_status check_options(const hw_options* o) {
   if (o->time_rule != 0 && o->time_rule != 1) return fail(HW_EINVAL, "time_rule must be 0 or 1");
   if (o->time_rule == 1 && o->positivity)
     return fail(HW_EINVAL, "the Gauss-Legendre time rule is not combined with the scale limiter");
-  if (o->step_kernels < 0 || o->step_kernels > 2) return fail(HW_EINVAL, "step_kernels must be 0, 1 or 2");
+  if (o->step_kernels < 0 || o->step_kernels > 3) return fail(HW_EINVAL, "step_kernels must be 0, 1, 2 or 3");
   return HW_OK;
 }
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -200,6 +213,7 @@ struct hw_solver {
   bool special_bc = false;   // the mesh has walls or inflow edges
   bool fused = false;        // steps run the fused reconstruct-and-flux kernel
   int fused_ntiles = 0;      // tiles of the fused step (0: tables not available)
+  int n_oedges = 0;          // edges of the edge-once flux phase (0: that phase is off)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -239,6 +253,9 @@ struct hw_solver {
     eq_params_finish(a.P);
     a.fused = FusedTiles{reinterpret_cast<const int32_t*>(ws + L.fslot), reinterpret_cast<const int32_t*>(ws + L.fhoff),
                          reinterpret_cast<const int32_t*>(ws + L.fhalo), fused_ntiles};
+    a.oedges = reinterpret_cast<const int32_t*>(ws + L.oedges);
+    a.n_oedges = n_oedges;
+    a.EP = n_oedges > 0 ? ws + L.EP : nullptr;
     return a;
   }
   // one step on stream st: the fused kernel, or reconstruction then flux
@@ -331,7 +348,7 @@ hw_status hw_workspace_bytes(const hw_mesh* mesh, const hw_options* opt, int32_t
   if (!mesh || !bytes) return fail(HW_EINVAL, "null pointer");
   if (hw_status s = check_options(opt)) return s;
   if (precision != HW_FP64 && precision != HW_FP32) return fail(HW_EINVAL, "unknown precision");
-  *bytes = make_layout(mesh->M.nt, ncomp(opt->eq), precision).total;
+  *bytes = make_layout(mesh->M.nt, ncomp(opt->eq), precision, edge_once_mode(opt, precision)).total;
   return HW_OK;
 }
 
@@ -368,7 +385,7 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
   s->N = M.nt;
   s->ld = padded_cells(M.nt);
   s->special_bc = M.special_bc;
-  s->L = make_layout(M.nt, s->m, precision);
+  s->L = make_layout(M.nt, s->m, precision, edge_once_mode(opt, precision));
   if (workspace_bytes < s->L.total) { delete s; return fail(HW_ENOMEM, "workspace smaller than hw_workspace_bytes"); }
   s->ws = static_cast<char*>(workspace);
   s->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -420,6 +437,23 @@ hw_status hw_state_init(const hw_mesh* mesh, const hw_options* opt, int32_t prec
       s->fused = s->opt.step_kernels == 2;
       if (s->fused) prepare_fused_kernel(precision, s->eq);
     }
+  }
+  // edge-once flux phase (step_kernels 3): every edge once, by its left cell
+  if (edge_once_mode(&s->opt, precision)) {
+    if (M.nt >= (int64_t(1) << 29)) return bail(fail(HW_EINVAL, "the edge-once flux phase takes fewer than 2^29 cells"));
+    std::vector<int32_t> oedges;
+    oedges.reserve((size_t)3 * M.nt);
+    const int32_t* nbe = M.igeo.data() + (size_t)I_NBE * M.nt;
+    for (int64_t i = 0; i < M.nt; ++i)
+      for (int j = 0; j < 3; ++j)
+        if ((nbe[i] >> (6 + j)) & 1) oedges.push_back((int32_t)(i * 4 + j));
+    if (!oedges.empty()) {
+      e = cudaMemcpyAsync(s->ws + s->L.oedges, oedges.data(), oedges.size() * 4, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);   // the host list goes out of scope
+      if (e != cudaSuccess) return bail(fail(HW_ECUDA, std::string("edge list: ") + cudaGetErrorString(e)));
+    }
+    s->n_oedges = (int)oedges.size();
+    prepare_edge_once_kernels(precision, s->eq);
   }
   // Look up the static scratch array of hw_step_static_scratch on this device
   // now: the lookup loads the module that holds the array, which commits its
@@ -595,7 +629,7 @@ hw_status hw_profile_read(hw_solver* s, double* ms, int64_t* nsteps) {
 
 hw_status hw_step_kernels(const hw_solver* s, int32_t* path) {
   if (!s || !path) return fail(HW_EINVAL, "null pointer");
-  *path = s->fused ? 2 : 1;
+  *path = s->fused ? 2 : s->n_oedges > 0 ? 3 : 1;
   return HW_OK;
 }
 

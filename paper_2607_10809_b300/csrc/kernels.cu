@@ -514,160 +514,144 @@ __device__ __forceinline__ R blend_theta(R gam, const R WL[4], const R WR[4], co
   return theta;
 }
 
-// Flux at the time nodes, cell-average and Green-Gauss update and CFL
-// candidates of up to kCells cells whose flux geometry, indices, state and
-// compensation words are staged in S (members geo, idx, lg, u, cc).  recs
-// gives the Taylor records: recs.mine(lc, q) of the cell's own point q,
-// recs.theirs(lc, j, nb, qn) the record of point qn of the neighbour nb
-// across edge j.  part, wn: shared scratch.
-template <typename R, int EQ, bool GL, bool LIM, typename Ctx, typename FS, typename Recs>
-__device__ __forceinline__ void flux_update_block(Ctx& ctx, int tile, int cell0, int count, const FS& S,
-                                                  const Recs& recs, const R* __restrict__ U, R* __restrict__ Un,
-                                                  R dtr, const EqParams& P, R (*part)[EqTraits<EQ>::m][6][kCells],
-                                                  R (*wn)[kCells]) {
+// LLF viscosity of an edge: the larger spectral radius of the flux Jacobian
+// along n at the two cells' averages (canonical left / right).
+template <typename R, int EQ>
+__device__ __forceinline__ R edge_alpha(const R* Wi, const R* Wn, bool left, R nx, R ny, const EqParams& P) {
+  R aL, aR;
+  if (left) { aL = spectral_radius_n<R, EQ>(Wi, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wn, nx, ny, P); }
+  else      { aL = spectral_radius_n<R, EQ>(Wn, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wi, nx, ny, P); }
+  return aL > aR ? aL : aR;
+}
+
+// One Gauss point of an edge: the LLF flux integrated over the time nodes
+// (Eq. flux; n outward of the edge's left cell) and the central value at
+// t_{n+1} (Eq. timeflux), from the Taylor records (W, W_t, W_tt) of the two
+// sides at that point.  mine: the calling cell's record; theirs: the other
+// cell's, or nullptr on a boundary edge, whose ghost record follows from
+// gtype (inflow: the imposed state; wall: the mirrored interior record;
+// transmissive: the interior record).  left: the calling cell is the edge's
+// left cell.
+template <typename R, int EQ, bool GL>
+__device__ __forceinline__ void edge_point_flux(const R* mine_src, const R* theirs_src, int gtype, bool left, R nx,
+                                                R ny, R alpha, R dtr, const EqParams& P, R* Fe, R* Sh) {
   constexpr int m = EqTraits<EQ>::m;
-  const int t = threadIdx.x;
-  {
-    const int lc = t % kCells, qp = t / kCells;
-    const bool act = lc < count;
-    const int j = qp >> 1, gm = qp & 1;
-    R Wi[m], Wn[m], Fe[m], Sh[m];
-    R nx = R(0), ny = R(0), el = R(0), alpha = R(0);
-    bool left = true;
-    int nb = -1;
-    if (act) {
-      nb = S.idx[j][lc];
-      const int je = (S.idx[3][lc] >> (2 * j)) & 3;
-      left = (S.idx[3][lc] >> (6 + j)) & 1;   // this cell owns the edge: canonical left side
-      nx = S.geo[2 * j][lc]; ny = S.geo[2 * j + 1][lc];
-      el = S.geo[6 + j][lc];
-      copy_rec<R, m>(Wi, S.u[lc]);
-      const int gtype = nb >= 0 ? kGhostTransmissive : ghost_type(S.idx[3][lc], j);
-      if (nb >= 0) {
-        copy_rec<R, m>(Wn, U + (size_t)nb * 3 * m);
-      } else {
-        // the ghost's average; a boundary edge belongs to its cell, so n is outward
+  R mine[3 * m], theirs[3 * m];
+  copy_rec<R, 3 * m>(mine, mine_src);
+  if (theirs_src) {
+    copy_rec<R, 3 * m>(theirs, theirs_src);
+  } else if (gtype == kGhostInflow) {   // the imposed state, constant in time
 #pragma unroll
-        for (int c = 0; c < m; ++c) {
-          R v, yv;
-          ghost_component<R, EQ>(gtype, S.u[lc], nx, ny, c, P, Wn[c], v, yv);
-        }
-      }
-      R aL, aR;
-      if (left) { aL = spectral_radius_n<R, EQ>(Wi, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wn, nx, ny, P); }
-      else      { aL = spectral_radius_n<R, EQ>(Wn, nx, ny, P); aR = spectral_radius_n<R, EQ>(Wi, nx, ny, P); }
-      alpha = aL > aR ? aL : aR;
-      // this cell's Taylor data at its point (j, gm); the neighbour's at the
-      // same physical point, its point (je, 1 - gm); canonical left / right
-      const int qm = 2 * j + gm, qn = 2 * je + (1 - gm);
-      R mine[3 * m], theirs[3 * m];
-      copy_rec<R, 3 * m>(mine, recs.mine(lc, qm));
-      if (nb >= 0) {
-        copy_rec<R, 3 * m>(theirs, recs.theirs(lc, j, nb, qn));
-      } else if (gtype == kGhostInflow) {   // the imposed state, constant in time
+    for (int c = 0; c < m; ++c) { theirs[c] = EqC<R>::win(P, c); theirs[m + c] = R(0); theirs[2 * m + c] = R(0); }
+  } else if (EQ == kEqEuler && gtype == kGhostWall) {   // the mirrored interior Taylor data
 #pragma unroll
-        for (int c = 0; c < m; ++c) { theirs[c] = EqC<R>::win(P, c); theirs[m + c] = R(0); theirs[2 * m + c] = R(0); }
-      } else if (EQ == kEqEuler && gtype == kGhostWall) {   // the mirrored interior Taylor data
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+      for (int c = 0; c < m; ++c) theirs[k * m + c] = mirror_c(nx, ny, mine + k * m, c);
+  } else {
+    copy_rec<R, 3 * m>(theirs, mine);   // transmissive: W^ext = W^int
+  }
+  R a0[m], a1[m], a2[m], b0[m], b1[m], b2[m];
 #pragma unroll
-          for (int c = 0; c < m; ++c) theirs[k * m + c] = mirror_c(nx, ny, mine + k * m, c);
-      } else {
-        copy_rec<R, 3 * m>(theirs, mine);   // transmissive: W^ext = W^int
-      }
-      R a0[m], a1[m], a2[m], b0[m], b1[m], b2[m];
+  for (int c = 0; c < m; ++c) {
+    a0[c] = left ? mine[c] : theirs[c];
+    a1[c] = left ? mine[m + c] : theirs[m + c];
+    a2[c] = left ? mine[2 * m + c] : theirs[2 * m + c];
+    b0[c] = left ? theirs[c] : mine[c];
+    b1[c] = left ? theirs[m + c] : mine[m + c];
+    b2[c] = left ? theirs[2 * m + c] : mine[2 * m + c];
+  }
+  constexpr int ns = GL ? 2 : 3;   // time nodes
+  R tau[3], wts[3];
+  if constexpr (GL) {
+    tau[0] = dtr * R(0.5 - kGaussNode); tau[1] = dtr * R(0.5 + kGaussNode);
+    wts[0] = R(0.5); wts[1] = R(0.5);
+  } else {
+    tau[0] = R(0); tau[1] = R(0.5) * dtr; tau[2] = dtr;
+    wts[0] = R(1.0 / 6.0); wts[1] = R(4.0 / 6.0); wts[2] = R(1.0 / 6.0);
+  }
 #pragma unroll
-      for (int c = 0; c < m; ++c) {
-        a0[c] = left ? mine[c] : theirs[c];
-        a1[c] = left ? mine[m + c] : theirs[m + c];
-        a2[c] = left ? mine[2 * m + c] : theirs[2 * m + c];
-        b0[c] = left ? theirs[c] : mine[c];
-        b1[c] = left ? theirs[m + c] : mine[m + c];
-        b2[c] = left ? theirs[2 * m + c] : mine[2 * m + c];
-      }
-      constexpr int ns = GL ? 2 : 3;   // time nodes
-      R tau[3], wts[3];
-      if constexpr (GL) {
-        tau[0] = dtr * R(0.5 - kGaussNode); tau[1] = dtr * R(0.5 + kGaussNode);
-        wts[0] = R(0.5); wts[1] = R(0.5);
-      } else {
-        tau[0] = R(0); tau[1] = R(0.5) * dtr; tau[2] = dtr;
-        wts[0] = R(1.0 / 6.0); wts[1] = R(4.0 / 6.0); wts[2] = R(1.0 / 6.0);
-      }
+  for (int c = 0; c < m; ++c) Fe[c] = R(0);
 #pragma unroll
-      for (int c = 0; c < m; ++c) Fe[c] = R(0);
+  for (int si = 0; si < ns; ++si) {
+    R WL[m], WR[m], HL[m], HR[m];
+    const R hs = R(0.5) * tau[si] * tau[si];
 #pragma unroll
-      for (int si = 0; si < ns; ++si) {
-        R WL[m], WR[m], HL[m], HR[m];
-        const R hs = R(0.5) * tau[si] * tau[si];
-#pragma unroll
-        for (int c = 0; c < m; ++c) {
-          WL[c] = a0[c] + tau[si] * a1[c] + hs * a2[c];
-          WR[c] = b0[c] + tau[si] * b1[c] + hs * b2[c];
-        }
-        flux_n<R, EQ>(WL, nx, ny, P, HL);
-        flux_n<R, EQ>(WR, nx, ny, P, HR);
-#pragma unroll
-        for (int c = 0; c < m; ++c) Fe[c] += wts[si] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
-        if (!GL && si == 2) {
-#pragma unroll
-          for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
-        }
-      }
-      if constexpr (GL) {   // Eq. timeflux from its own Taylor evaluation at t_{n+1}
-        const R hs = R(0.5) * dtr * dtr;
-#pragma unroll
-        for (int c = 0; c < m; ++c)
-          Sh[c] = R(0.5) * ((a0[c] + dtr * a1[c] + hs * a2[c]) + (b0[c] + dtr * b1[c] + hs * b2[c]));
-      }
+    for (int c = 0; c < m; ++c) {
+      WL[c] = a0[c] + tau[si] * a1[c] + hs * a2[c];
+      WR[c] = b0[c] + tau[si] * b1[c] + hs * b2[c];
     }
-    if constexpr (LIM) {
-      // flux blending: the edge's high-order flux is the mean of its two
-      // Gauss points' (the same sum on both sides of the edge)
-      if (act) {
+    flux_n<R, EQ>(WL, nx, ny, P, HL);
+    flux_n<R, EQ>(WR, nx, ny, P, HR);
 #pragma unroll
-        for (int c = 0; c < m; ++c) part[0][c][qp][lc] = Fe[c];
-      }
-      __syncthreads();
-      if (act) {
-        R FH[4], FL[4], WL[4], WR[4], HL[4], HR[4];
+    for (int c = 0; c < m; ++c) Fe[c] += wts[si] * (R(0.5) * (HR[c] + HL[c] - alpha * (WR[c] - WL[c])));
+    if (!GL && si == 2) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          FH[c] = R(0.5) * (part[0][c][2 * j][lc] + part[0][c][2 * j + 1][lc]);
-          WL[c] = left ? Wi[c] : Wn[c];
-          WR[c] = left ? Wn[c] : Wi[c];
-        }
-        flux_n<R, EQ>(WL, nx, ny, P, HL);
-        flux_n<R, EQ>(WR, nx, ny, P, HR);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) FL[c] = R(0.5) * (HL[c] + HR[c] - alpha * (WR[c] - WL[c]));
-        const R pown = S.lg[0][lc], pnb = S.lg[1 + j][lc];
-        const R lamL = dtr * (left ? pown : pnb);
-        const R lamR = nb >= 0 ? dtr * (left ? pnb : pown) : R(-1);
-        const R theta = blend_theta(EqC<R>::gam(P), WL, WR, HL, HR, FL, FH, lamL, lamR);
-        if (theta < R(1)) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) Fe[c] = FL[c] + theta * (Fe[c] - FL[c]);
-        }
-      }
-      __syncthreads();
-    }
-    if (act) {
-      // Gauss weight 1/2 and the cell's outward normal (+-n).  In FP32 the
-      // Green-Gauss terms are taken relative to the cell's own average: the
-      // cell's |e| n sum to zero, so the result is the same, while the terms
-      // shrink from |W| / h to |grad W| and their rounding with them.
-      const R sgn = left ? R(0.5) * el : R(-0.5) * el;
-#pragma unroll
-      for (int c = 0; c < m; ++c) {
-        const R sh = sizeof(R) == 4 ? Sh[c] - Wi[c] : Sh[c];
-        part[0][c][qp][lc] = sgn * Fe[c];
-        part[1][c][qp][lc] = sgn * nx * sh;
-        part[2][c][qp][lc] = sgn * ny * sh;
-      }
+      for (int c = 0; c < m; ++c) Sh[c] = R(0.5) * (WL[c] + WR[c]);   // Eq. timeflux
     }
   }
-  __syncthreads();
+  if constexpr (GL) {   // Eq. timeflux from its own Taylor evaluation at t_{n+1}
+    const R hs = R(0.5) * dtr * dtr;
+#pragma unroll
+    for (int c = 0; c < m; ++c)
+      Sh[c] = R(0.5) * ((a0[c] + dtr * a1[c] + hs * a2[c]) + (b0[c] + dtr * b1[c] + hs * b2[c]));
+  }
+}
+
+// Flux blending of one Gauss point (Euler, scale limiter): FH is the mean of
+// the edge's two Gauss-point fluxes, pown / pnb the perimeter over area of
+// the calling cell and of the other one (has_nb false: a boundary edge).
+template <typename R, int EQ>
+__device__ __forceinline__ void blend_point(const R* Wi, const R* Wn, bool left, bool has_nb, R nx, R ny, R alpha,
+                                            const R* FH, R pown, R pnb, R dtr, const EqParams& P, R* Fe) {
+  R FL[4], WL[4], WR[4], HL[4], HR[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    WL[c] = left ? Wi[c] : Wn[c];
+    WR[c] = left ? Wn[c] : Wi[c];
+  }
+  flux_n<R, EQ>(WL, nx, ny, P, HL);
+  flux_n<R, EQ>(WR, nx, ny, P, HR);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) FL[c] = R(0.5) * (HL[c] + HR[c] - alpha * (WR[c] - WL[c]));
+  const R lamL = dtr * (left ? pown : pnb);
+  const R lamR = has_nb ? dtr * (left ? pnb : pown) : R(-1);
+  const R theta = blend_theta(EqC<R>::gam(P), WL, WR, HL, HR, FL, FH, lamL, lamR);
+  if (theta < R(1)) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Fe[c] = FL[c] + theta * (Fe[c] - FL[c]);
+  }
+}
+
+// Green-Gauss and flux shares of one (cell, point) into part: Gauss weight
+// 1/2 and the cell's outward normal (+-n).  In FP32 the Green-Gauss terms are
+// taken relative to the cell's own average: the cell's |e| n sum to zero, so
+// the result is the same, while the terms shrink from |W| / h to |grad W| and
+// their rounding with them.
+template <typename R, int m>
+__device__ __forceinline__ void point_shares(bool left, R el, R nx, R ny, const R* Fe, const R* Sh, const R* Wi,
+                                             int qp, int lc, R (*part)[m][6][kCells]) {
+  const R sgn = left ? R(0.5) * el : R(-0.5) * el;
+#pragma unroll
+  for (int c = 0; c < m; ++c) {
+    const R sh = sizeof(R) == 4 ? Sh[c] - Wi[c] : Sh[c];
+    part[0][c][qp][lc] = sgn * Fe[c];
+    part[1][c][qp][lc] = sgn * nx * sh;
+    part[2][c][qp][lc] = sgn * ny * sh;
+  }
+}
+
+// After the shares of a tile are in part (and a barrier): the six-way sums,
+// the cell-average update (compensated in FP32) and the new derivative
+// averages into Un, the CFL candidates of the new averages; ends with a
+// barrier.  S: the tile's staged state (u), compensation words (cc) and flux
+// geometry (geo, planes G_NRM ..).
+template <typename R, int EQ, typename Ctx, typename FS>
+__device__ __forceinline__ void sum_update_cfl(Ctx& ctx, int tile, int cell0, int count, const FS& S,
+                                               R* __restrict__ Un, R dtr, const EqParams& P,
+                                               R (*part)[EqTraits<EQ>::m][6][kCells], R (*wn)[kCells]) {
+  constexpr int m = EqTraits<EQ>::m;
+  const int t = threadIdx.x;
   // sums of the six shares: thread (cell, output) for the 3m outputs
   for (int k = t; k < 3 * m * kCells; k += kThreads) {
     const int lc = k % kCells, o = k / kCells;   // o = kind * m + c
@@ -712,6 +696,74 @@ __device__ __forceinline__ void flux_update_block(Ctx& ctx, int tile, int cell0,
     ctx.tile_min(tile, v);
   }
   __syncthreads();
+}
+
+// Flux at the time nodes, cell-average and Green-Gauss update and CFL
+// candidates of up to kCells cells whose flux geometry, indices, state and
+// compensation words are staged in S (members geo, idx, lg, u, cc).  recs
+// gives the Taylor records: recs.mine(lc, q) of the cell's own point q,
+// recs.theirs(lc, j, nb, qn) the record of point qn of the neighbour nb
+// across edge j.  part, wn: shared scratch.
+template <typename R, int EQ, bool GL, bool LIM, typename Ctx, typename FS, typename Recs>
+__device__ __forceinline__ void flux_update_block(Ctx& ctx, int tile, int cell0, int count, const FS& S,
+                                                  const Recs& recs, const R* __restrict__ U, R* __restrict__ Un,
+                                                  R dtr, const EqParams& P, R (*part)[EqTraits<EQ>::m][6][kCells],
+                                                  R (*wn)[kCells]) {
+  constexpr int m = EqTraits<EQ>::m;
+  const int t = threadIdx.x;
+  {
+    const int lc = t % kCells, qp = t / kCells;
+    const bool act = lc < count;
+    const int j = qp >> 1, gm = qp & 1;
+    R Wi[m], Wn[m], Fe[m], Sh[m];
+    R nx = R(0), ny = R(0), el = R(0), alpha = R(0);
+    bool left = true;
+    int nb = -1;
+    if (act) {
+      nb = S.idx[j][lc];
+      const int je = (S.idx[3][lc] >> (2 * j)) & 3;
+      left = (S.idx[3][lc] >> (6 + j)) & 1;   // this cell owns the edge: canonical left side
+      nx = S.geo[2 * j][lc]; ny = S.geo[2 * j + 1][lc];
+      el = S.geo[6 + j][lc];
+      copy_rec<R, m>(Wi, S.u[lc]);
+      const int gtype = nb >= 0 ? kGhostTransmissive : ghost_type(S.idx[3][lc], j);
+      if (nb >= 0) {
+        copy_rec<R, m>(Wn, U + (size_t)nb * 3 * m);
+      } else {
+        // the ghost's average; a boundary edge belongs to its cell, so n is outward
+#pragma unroll
+        for (int c = 0; c < m; ++c) {
+          R v, yv;
+          ghost_component<R, EQ>(gtype, S.u[lc], nx, ny, c, P, Wn[c], v, yv);
+        }
+      }
+      alpha = edge_alpha<R, EQ>(Wi, Wn, left, nx, ny, P);
+      // this cell's Taylor data at its point (j, gm); the neighbour's at the
+      // same physical point, its point (je, 1 - gm); canonical left / right
+      const int qm = 2 * j + gm, qn = 2 * je + (1 - gm);
+      edge_point_flux<R, EQ, GL>(recs.mine(lc, qm), nb >= 0 ? recs.theirs(lc, j, nb, qn) : nullptr, gtype, left, nx,
+                                 ny, alpha, dtr, P, Fe, Sh);
+    }
+    if constexpr (LIM) {
+      // flux blending: the edge's high-order flux is the mean of its two
+      // Gauss points' (the same sum on both sides of the edge)
+      if (act) {
+#pragma unroll
+        for (int c = 0; c < m; ++c) part[0][c][qp][lc] = Fe[c];
+      }
+      __syncthreads();
+      if (act) {
+        R FH[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) FH[c] = R(0.5) * (part[0][c][2 * j][lc] + part[0][c][2 * j + 1][lc]);
+        blend_point<R, EQ>(Wi, Wn, left, nb >= 0, nx, ny, alpha, FH, S.lg[0][lc], S.lg[1 + j][lc], dtr, P, Fe);
+      }
+      __syncthreads();
+    }
+    if (act) point_shares<R, m>(left, el, nx, ny, Fe, Sh, Wi, qp, lc, part);
+  }
+  __syncthreads();
+  sum_update_cfl<R, EQ>(ctx, tile, cell0, count, S, Un, dtr, P, part, wn);
 }
 
 // Edge-point records of a tile staged in an EdgeStage (own) and in global
@@ -854,6 +906,182 @@ __global__ void __launch_bounds__(kThreads, edge_min_blocks<R, EQ>()) k_edge(con
   __syncthreads();
   unsigned ph[2] = {0u, 0u};
   if (!edge_phase<R, EQ, GL, LIM>(ctx, &mEgeo, &mIdx, &mLgeo, P, Pb, base, bar, ph)) ctx.local_min = dinf();
+  finish_step(sc, ctx.local_min, dt, true);
+}
+
+// ---------------------------------------------------------------- edge-once flux phase
+// The two-kernel flux phase evaluates each edge once instead of once per
+// cell: k_edge_flux, one thread per edge (listed by its left, owning cell),
+// computes both Gauss points' time-integrated flux and central value (with
+// the flux blending of the scale limiter) into EP; k_edge_update then runs the
+// update of every cell (shares of its six points, read from its own slots or
+// from the neighbour's slot of the same point, sums, update, CFL).  The values
+// are those the owning cell computes in k_edge, so both paths give the same
+// bits; this one does half the flux arithmetic, which pays where the FP64
+// pipe bounds the step.
+constexpr int kFluxThreads = 128;
+
+template <typename R, int EQ, bool GL, bool LIM>
+__global__ void __launch_bounds__(kFluxThreads) k_edge_flux(GeoView<R> G, const R* __restrict__ U,
+                                                            const R* __restrict__ Pb, R* __restrict__ EP,
+                                                            const int32_t* __restrict__ oedges, int ne, EqParams P,
+                                                            DevScalars* sc, double dt_fixed) {
+  constexpr int m = EqTraits<EQ>::m;
+  static_assert(!LIM || EQ == kEqEuler, "flux blending is for the Euler equations");
+  const volatile DevScalars* vs = sc;
+  if (vs->done) return;
+  const R dtr = R(dt_fixed > 0 ? dt_fixed : vs->dt);
+  for (int e = blockIdx.x * kFluxThreads + threadIdx.x; e < ne; e += gridDim.x * kFluxThreads) {
+    const int code = oedges[e], i = code >> 2, j = code & 3;
+    const int nb = G.n(I_NBR + j, i), packed = G.n(I_NBE, i);
+    const int je = (packed >> (2 * j)) & 3;
+    const R nx = G.r(G_NRM + 2 * j, i), ny = G.r(G_NRM + 2 * j + 1, i);
+    const R* ui = U + (size_t)i * 3 * m;
+    R Wi[m], Wn[m];
+    copy_rec<R, m>(Wi, ui);
+    const int gtype = nb >= 0 ? kGhostTransmissive : ghost_type(packed, j);
+    if (nb >= 0) {
+      copy_rec<R, m>(Wn, U + (size_t)nb * 3 * m);
+    } else {
+#pragma unroll
+      for (int c = 0; c < m; ++c) {
+        R v, yv;
+        ghost_component<R, EQ>(gtype, ui, nx, ny, c, P, Wn[c], v, yv);
+      }
+    }
+    const R alpha = edge_alpha<R, EQ>(Wi, Wn, true, nx, ny, P);
+    R Fe[2][m], Sh[2][m];
+#pragma unroll
+    for (int gm = 0; gm < 2; ++gm)
+      edge_point_flux<R, EQ, GL>(Pb + (size_t)i * 18 * m + (2 * j + gm) * 3 * m,
+                                 nb >= 0 ? Pb + (size_t)nb * 18 * m + (2 * je + 1 - gm) * 3 * m : nullptr, gtype,
+                                 true, nx, ny, alpha, dtr, P, Fe[gm], Sh[gm]);
+    if constexpr (LIM) {
+      R FH[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) FH[c] = R(0.5) * (Fe[0][c] + Fe[1][c]);
+      const R pown = G.r(G_PK, i), pnb = G.r(G_PN + j, i);
+#pragma unroll
+      for (int gm = 0; gm < 2; ++gm)
+        blend_point<R, EQ>(Wi, Wn, true, nb >= 0, nx, ny, alpha, FH, pown, pnb, dtr, P, Fe[gm]);
+    }
+#pragma unroll
+    for (int gm = 0; gm < 2; ++gm) {
+      R* out = EP + ((size_t)i * 6 + 2 * j + gm) * 2 * m;
+#pragma unroll
+      for (int c = 0; c < m; ++c) { out[c] = Fe[gm][c]; out[m + c] = Sh[gm][c]; }
+    }
+  }
+}
+
+template <typename R, int EQ> struct UpdStage {
+  static constexpr int m = EqTraits<EQ>::m;
+  R geo[kEdgePlanes][kCells];    // TMA tensor box: planes x cells
+  int32_t idx[4][kCells];        // TMA tensor box
+  R u[kCells][3 * m];            // bulk copy of the tile's state records
+  R cc[kCells][m];               // bulk copy of the compensation words (FP32 form; else unused)
+};
+static_assert(sizeof(UpdStage<float, 2>) % 128 == 0 && sizeof(UpdStage<double, 2>) % 128 == 0 &&
+                  sizeof(UpdStage<float, 0>) % 128 == 0 && sizeof(UpdStage<double, 0>) % 128 == 0,
+              "every stage starts 128-byte aligned (TMA destination)");
+
+template <typename R, int EQ> constexpr size_t update_smem_bytes() {
+  return 2 * sizeof(UpdStage<R, EQ>) + sizeof(R) * 3 * EqTraits<EQ>::m * 6 * kCells +
+         sizeof(R) * EqTraits<EQ>::m * kCells + 2 * sizeof(uint64_t) + 128;
+}
+
+template <typename R, int EQ>
+__global__ void __launch_bounds__(kThreads) k_edge_update(const __grid_constant__ CUtensorMap mEgeo,
+                                                          const __grid_constant__ CUtensorMap mIdx, GeoView<R> G,
+                                                          const R* __restrict__ U, R* __restrict__ Un,
+                                                          const R* __restrict__ EP, R* C, EqParams P, DevScalars* sc,
+                                                          double dt_fixed, TileSet ts) {
+  constexpr int m = EqTraits<EQ>::m;
+  using Stage = UpdStage<R, EQ>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  Stage* st = reinterpret_cast<Stage*>(base);
+  R (*part)[m][6][kCells] = reinterpret_cast<R (*)[m][6][kCells]>(base + 2 * sizeof(Stage));
+  R (*wn)[kCells] = reinterpret_cast<R (*)[kCells]>(base + 2 * sizeof(Stage) + sizeof(R) * 3 * m * 6 * kCells);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + update_smem_bytes<R, EQ>() - 128 - 2 * sizeof(uint64_t));
+  const int N = G.N;
+  const int t = threadIdx.x;
+  const volatile DevScalars* vs = sc;
+  if (vs->done) {  // target reached: keep the state, preserving the buffer alternation
+    for (int tile = blockIdx.x; tile < ts.ntiles; tile += gridDim.x) {
+      int cell0, count;
+      tile_range(ts, N, tile, cell0, count);
+      for (int k = t; k < 3 * m * count; k += kThreads) Un[(size_t)cell0 * 3 * m + k] = U[(size_t)cell0 * 3 * m + k];
+    }
+    return;
+  }
+  const double dt = dt_fixed > 0 ? dt_fixed : vs->dt;
+  const R dtr = R(dt);
+  SingleCtx<R> ctx{ts, N, U, Un, dt, sc, dinf(), C};
+  if (t == 0) {
+    prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  constexpr unsigned kBytes = sizeof(Stage);
+  auto issue = [&](int sidx, int tile) {
+    int c0, cnt;
+    tile_range(ts, N, tile, c0, cnt);
+    mbar_arrive_expect_tx(&bar[sidx], kBytes - (C ? 0u : (unsigned)sizeof(Stage::cc)));
+    tma_load_2d(&st[sidx].geo[0][0], &mEgeo, c0, 0, &bar[sidx]);
+    tma_load_2d(&st[sidx].idx[0][0], &mIdx, c0, 0, &bar[sidx]);
+    bulk_load(&st[sidx].u[0][0], U + (size_t)c0 * 3 * m, kCells * 3 * m * sizeof(R), &bar[sidx]);
+    if (C) bulk_load(&st[sidx].cc[0][0], C + (size_t)c0 * m, kCells * m * sizeof(R), &bar[sidx]);
+  };
+  unsigned ph[2] = {0u, 0u};
+  int tile = blockIdx.x;
+  if (t == 0 && tile < ts.ntiles) {
+    fence_proxy_async();
+    issue(0, tile);
+  }
+  bool ok = true;
+  for (int s = 0; tile < ts.ntiles; s ^= 1) {
+    const int next = tile + gridDim.x;
+    if (t == 0 && next < ts.ntiles) {
+      fence_proxy_async();
+      issue(s ^ 1, next);
+    }
+    const bool w = mbar_wait(&bar[s], ph[s]);
+    ph[s] ^= 1u;
+    if (__syncthreads_or(!w)) {
+      if (t == 0) {
+        ctx.flag(2u);
+        if (next < ts.ntiles && mbar_wait(&bar[s ^ 1], ph[s ^ 1])) ph[s ^ 1] ^= 1u;   // drain the copy in flight
+      }
+      ok = false;
+      break;
+    }
+    int cell0, count;
+    tile_range(ts, N, tile, cell0, count);
+    const Stage& S = st[s];
+    {
+      const int lc = t % kCells, qp = t / kCells;
+      if (lc < count) {
+        const int j = qp >> 1, gm = qp & 1;
+        const int nb = S.idx[j][lc];
+        const int je = (S.idx[3][lc] >> (2 * j)) & 3;
+        const bool left = (S.idx[3][lc] >> (6 + j)) & 1;
+        // this point's values: the cell's own slot if it owns the edge, else
+        // the neighbour's slot of the same physical point (its point (je, 1 - gm))
+        const size_t slot = left ? (size_t)(cell0 + lc) * 6 + qp : (size_t)nb * 6 + 2 * je + (1 - gm);
+        R FS[2 * m];
+        copy_rec<R, 2 * m>(FS, EP + slot * 2 * m);
+        point_shares<R, m>(left, S.geo[6 + j][lc], S.geo[2 * j][lc], S.geo[2 * j + 1][lc], FS, FS + m, S.u[lc], qp,
+                           lc, part);
+      }
+    }
+    __syncthreads();
+    sum_update_cfl<R, EQ>(ctx, tile, cell0, count, S, Un, dtr, P, part, wn);
+    tile = next;
+  }
+  if (!ok) ctx.local_min = dinf();
   finish_step(sc, ctx.local_min, dt, true);
 }
 
@@ -1368,15 +1596,46 @@ template <typename R, int EQ, bool GL, bool LIM> void launch_edge_rule(const Ste
       a.maps->egeo, a.maps->idx, a.maps->lgeo, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
       reinterpret_cast<const R*>(a.Pb), reinterpret_cast<R*>(a.C), a.P, a.sc, a.dt_fixed, a.tiles);
 }
+template <typename R, int EQ, bool GL, bool LIM> int flux_cap() {
+  static const int cap = resident_blocks(k_edge_flux<R, EQ, GL, LIM>, kFluxThreads, 0);
+  return cap;
+}
+template <typename R, int EQ> int update_cap() {
+  static const int cap = resident_blocks(k_edge_update<R, EQ>, kThreads, update_smem_bytes<R, EQ>());
+  return cap;
+}
+template <typename R, int EQ, bool GL, bool LIM> void launch_edge_once(const StepArgs& a, cudaStream_t st) {
+  GeoView<R> G{reinterpret_cast<const R*>(a.rgeo), a.igeo, a.N, a.ld};
+  const int nb = (a.n_oedges + kFluxThreads - 1) / kFluxThreads, fc = flux_cap<R, EQ, GL, LIM>();
+  k_edge_flux<R, EQ, GL, LIM><<<nb < fc ? (nb > 0 ? nb : 1) : fc, kFluxThreads, 0, st>>>(
+      G, reinterpret_cast<const R*>(a.U), reinterpret_cast<const R*>(a.Pb), reinterpret_cast<R*>(a.EP), a.oedges,
+      a.n_oedges, a.P, a.sc, a.dt_fixed);
+  const int nt = a.tiles.ntiles, uc = update_cap<R, EQ>();
+  k_edge_update<R, EQ><<<nt < uc ? (nt > 0 ? nt : 1) : uc, kThreads, update_smem_bytes<R, EQ>(), st>>>(
+      a.maps->egeo, a.maps->idx, G, reinterpret_cast<const R*>(a.U), reinterpret_cast<R*>(a.Un),
+      reinterpret_cast<const R*>(a.EP), reinterpret_cast<R*>(a.C), a.P, a.sc, a.dt_fixed, a.tiles);
+}
 template <typename R, int EQ> void launch_edge_t(const StepArgs& a, cudaStream_t st) {
   if constexpr (EQ == kEqEuler) {
     if (a.P.positivity) {   // the Gauss-Legendre rule is refused with the limiter
-      launch_edge_rule<R, EQ, false, true>(a, st);
+      if (a.EP) launch_edge_once<R, EQ, false, true>(a, st);
+      else launch_edge_rule<R, EQ, false, true>(a, st);
       return;
     }
   }
-  if (a.P.time_rule == 1) launch_edge_rule<R, EQ, true, false>(a, st);
-  else launch_edge_rule<R, EQ, false, false>(a, st);
+  if (a.P.time_rule == 1) {
+    if (a.EP) launch_edge_once<R, EQ, true, false>(a, st);
+    else launch_edge_rule<R, EQ, true, false>(a, st);
+  } else {
+    if (a.EP) launch_edge_once<R, EQ, false, false>(a, st);
+    else launch_edge_rule<R, EQ, false, false>(a, st);
+  }
+}
+template <typename R, int EQ> void prepare_edge_once_t() {
+  (void)flux_cap<R, EQ, false, false>();
+  (void)flux_cap<R, EQ, true, false>();
+  if constexpr (EQ == kEqEuler) (void)flux_cap<R, EQ, false, true>();
+  (void)update_cap<R, EQ>();
 }
 template <typename R> struct FusedShape {
   static constexpr int TT = sizeof(R) == 4 ? kFusedTile32 : kFusedTile64;
@@ -1440,6 +1699,7 @@ void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st) {
 void launch_cfl(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_cfl_t, prec, eq, a, st); }
 void launch_fused(int prec, int eq, const StepArgs& a, cudaStream_t st) { HW_DISPATCH(launch_fused_t, prec, eq, a, st); }
 void prepare_fused_kernel(int prec, int eq) { HW_DISPATCH(prepare_fused_t, prec, eq); }
+void prepare_edge_once_kernels(int prec, int eq) { HW_DISPATCH(prepare_edge_once_t, prec, eq); }
 
 void launch_reset(DevScalars* sc, double t, double cfl, cudaStream_t st) { k_reset<<<1, 32, 0, st>>>(sc, t, cfl); }
 

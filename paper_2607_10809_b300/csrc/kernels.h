@@ -90,6 +90,13 @@ struct StepArgs {
   double dt_fixed;         // > 0: use this step instead of the device CFL step
   EqParams P;
   FusedTiles fused;        // tables of the fused step (ntiles = 0: not available)
+  // edge-once flux phase (EP non-null): oedges lists the n_oedges edges by
+  // their left (owning) cell, i * 4 + j in internal order; EP [ld][6][2m]
+  // receives the owner's time-integrated flux and central value per Gauss
+  // point, which both cells of the edge then read
+  const int32_t* oedges;
+  int n_oedges;
+  void* EP;
 };
 
 // Arguments of the batched persistent kernel.
@@ -143,6 +150,7 @@ void launch_batch_reset_ctl(BatchCtl* ctl, cudaStream_t st);
 // Sets the kernels' shared-memory limits and caches their resident-block
 // counts; call once per (precision, equation) before any stream capture.
 void prepare_step_kernels(int prec, int eq);
+void prepare_edge_once_kernels(int prec, int eq);
 void launch_recon(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_edge(int prec, int eq, const StepArgs& a, cudaStream_t st);
 void launch_step(int prec, int eq, const StepArgs& a, cudaStream_t st);

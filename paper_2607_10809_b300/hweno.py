@@ -133,7 +133,7 @@ def _ptr(a):
 
 
 TIME_RULES = {"lobatto": 0, "gauss": 1}
-STEP_KERNELS = {"default": 0, "separate": 1, "fused": 2}
+STEP_KERNELS = {"default": 0, "separate": 1, "fused": 2, "edge_once": 3}
 
 
 def options(eq="advection", a=(1.0, 1.0), gamma_gas=1.4, cfl=0.5, gamma_lin=(0.94, 0.02, 0.02, 0.02), eps=1e-8,
@@ -344,10 +344,10 @@ class Solver:
                                       ctypes.c_void_p(scratch.data_ptr()), scratch.numel()))
 
     def step_kernels(self):
-        """'fused' or 'separate': the kernels this solver's steps run."""
+        """'separate', 'fused' or 'edge_once': the kernels this solver's steps run."""
         p = ctypes.c_int32()
         _check(load().hw_step_kernels(self.h, ctypes.byref(p)))
-        return "fused" if p.value == 2 else "separate"
+        return {1: "separate", 2: "fused", 3: "edge_once"}[p.value]
 
     def profile(self, enable=True):
         _check(load().hw_profile(self.h, int(enable)))

@@ -107,11 +107,13 @@ def test_fused_agrees_with_separate_kernels(precision):
     assert err < (FP64_TOL if precision == "fp64" else 1e-5)
 
 
-def test_default_is_the_two_kernel_step():
+def test_default_step_kernels():
+    """The default step: the two-sided flux kernel in FP32, the edge-once flux
+    phase in FP64 (where the FP64 pipe bounds the step)."""
     mesh = I.jittered_periodic(12, 10.0, 0.15, seed=3)
     U0 = I.initial_state(mesh, I.vortex, 4)
-    for prec in ("fp32", "fp64"):
-        assert hweno.Solver(mesh, U0, eq="euler", precision=prec).step_kernels() == "separate"
+    for prec, path in (("fp32", "separate"), ("fp64", "edge_once")):
+        assert hweno.Solver(mesh, U0, eq="euler", precision=prec).step_kernels() == path
 
 
 def test_fused_conservation_and_steps_past_the_target():
