@@ -308,6 +308,10 @@ typedef struct {
   int32_t steps_per_launch;  /* time steps per launch (graph replay) at most */
   int32_t withhold_block;    /* testing only: this block withholds its first barrier arrival (-1: none) */
   int64_t spin_limit;        /* polls of a barrier wait before giving up; 0 = default (about 2 s) */
+  int32_t launch_mode;       /* 0: each chunk of steps in one persistent cooperative launch with grid
+                                barriers (blocks_per_sm applies); 1: every step as three launches
+                                (reconstruction, flux/update, per-solve finish) captured in one graph,
+                                each kernel at its own occupancy.  Same results bit for bit. */
 } hw_batch_schedule;
 
 void hw_batch_schedule_default(hw_batch_schedule* s);
@@ -323,7 +327,8 @@ hw_status hw_batch_create(const hw_mesh* const* meshes, int32_t n, const hw_opti
 hw_status hw_batch_set_schedule(hw_batch* b, const hw_batch_schedule* s);
 /* Current schedule and the grid it launches (blocks). */
 hw_status hw_batch_get_schedule(const hw_batch* b, hw_batch_schedule* s, int32_t* grid_blocks);
-/* Time every candidate schedule (tile order x blocks per SM) on trial_steps
+/* Time every candidate schedule (launch mode 0 with each tile order and each
+ * number of blocks per SM, launch mode 1 with each tile order) on trial_steps
  * steps from the initial state, keep the fastest, restore the initial state.
  * best / best_ms may be NULL. */
 hw_status hw_batch_autotune(hw_batch* b, int32_t trial_steps, hw_batch_schedule* best, double* best_ms);

@@ -199,7 +199,13 @@ hw_status capture_graph(hw_batch* b, int steps) {
   cudaGraph_t g = nullptr;
   HB_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   launch_batch_reset_ctl(b->ctl(), b->cap_stream);
-  cudaError_t e = launch_batch(b->prec, b->eq, b->args(steps), b->cap_stream);
+  cudaError_t e = cudaSuccess;
+  if (b->sched.launch_mode == 1) {   // three launches per step; a finished solve's tiles are skipped
+    const BatchArgs a = b->args(steps);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = launch_batch_step(b->prec, b->eq, a, k & 1, b->cap_stream);
+  } else {                           // one persistent cooperative launch with grid barriers
+    e = launch_batch(b->prec, b->eq, b->args(steps), b->cap_stream);
+  }
   cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -240,6 +246,7 @@ void hw_batch_schedule_default(hw_batch_schedule* s) {
   s->steps_per_launch = 1 << 20;
   s->spin_limit = 0;         // 0: default
   s->withhold_block = -1;
+  s->launch_mode = 0;
 }
 
 hw_status hw_batch_workspace_bytes(const hw_mesh* const* meshes, int32_t n, const hw_options* opt, int32_t precision,
@@ -360,8 +367,11 @@ hw_status hw_batch_create(const hw_mesh* const* meshes, int32_t n, const hw_opti
 
 hw_status hw_batch_set_schedule(hw_batch* b, const hw_batch_schedule* s) {
   if (!b || !s) return bfail(HW_EINVAL, "null pointer");
-  if (s->tile_order < 0 || s->tile_order > 2 || s->blocks_per_sm < 0 || s->steps_per_launch <= 0)
+  if (s->tile_order < 0 || s->tile_order > 2 || s->blocks_per_sm < 0 || s->steps_per_launch <= 0 ||
+      s->launch_mode < 0 || s->launch_mode > 1)
     return bfail(HW_EINVAL, "bad schedule");
+  if (s->launch_mode == 1 && s->withhold_block >= 0)
+    return bfail(HW_EINVAL, "withhold_block tests the grid barrier of launch_mode 0");
   const bool order_changed = s->tile_order != b->sched.tile_order;
   b->sched = *s;
   if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
@@ -454,11 +464,14 @@ hw_status hw_batch_autotune(hw_batch* b, int32_t trial_steps, hw_batch_schedule*
   const int per_sm = batch_blocks_per_sm(b->prec, b->eq, b->eq == HW_EULER && b->opt.positivity);
   hw_batch_schedule base = b->sched, pick = b->sched;
   double pick_ms = 1e300;
+  for (int mode = 0; mode <= 1; ++mode)
   for (int order = 0; order <= 2; ++order)
-    for (int bps = 1; bps <= per_sm; ++bps) {
+    for (int bps = 1; bps <= (mode == 0 ? per_sm : 1); ++bps) {   // the three-launch form sizes its own grids
       hw_batch_schedule s = base;
+      s.launch_mode = mode;
+      s.withhold_block = -1;
       s.tile_order = order;
-      s.blocks_per_sm = bps;
+      s.blocks_per_sm = mode == 0 ? bps : 0;
       s.steps_per_launch = trial_steps;
       if (hw_status st = hw_batch_set_schedule(b, &s)) return st;
       if (hw_status st = hw_batch_reset(b)) return st;

@@ -1328,6 +1328,35 @@ __device__ bool grid_barrier(BatchCtl* ctl, unsigned long long spin_limit, bool 
 #endif
 template <typename R> constexpr int batch_min_blocks() { return sizeof(R) == 4 ? HW_BATCH_MIN_BLOCKS : 1; }
 
+// End of a batched step, thread gid for solve gid: time, step count, status
+// and next time step of every running solve (its CFL minimum taken over the
+// step's tiles); counts the solves still running in active[slot].
+__device__ __forceinline__ void batch_finish_step(BatchSolve* bs, BatchCtl* ctl, int gid, int nsolves, double cfl,
+                                                  int slot) {
+  if (gid < nsolves) {
+    volatile BatchSolve* b = &bs[gid];
+    if (!b->done) {
+      const double tn = b->t + b->dt;
+      b->t = tn;
+      b->nsteps = b->nsteps + 1;
+      const double mn = __longlong_as_double((long long)atomicAdd(&bs[gid].lam_min_bits, 0ull));
+      double dtn = cfl * mn;
+      int done = 0;
+      if (b->failed) done = 1;
+      else if (tn >= b->T * (1.0 - 1e-14)) done = 1;
+      else if (tn + dtn > b->T) dtn = b->T - tn;
+      b->dt = dtn;
+      b->done = done;
+      atomicExch(&bs[gid].lam_min_bits, dbits(dinf()));
+      if (!done) atomicAdd(&ctl->active[slot], 1u);
+    }
+  }
+  if (gid == 0) {
+    atomicExch(&ctl->active[slot ^ 1], 0u);
+    atomicAdd(&ctl->steps_run, 1);
+  }
+}
+
 template <typename R, int EQ, bool LIM>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks<R>()) k_batch(const __grid_constant__ CUtensorMap mGeo,
                                                      const __grid_constant__ CUtensorMap mEgeo,
@@ -1362,33 +1391,55 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks<R>()) k_batch(const
     ok = edge_phase<R, EQ, false, LIM>(ctx, &mEgeo, &mIdx, &mLgeo, P, Pb, base, bar, ph);
     if (!grid_barrier(ctl, spin_limit, !ok)) ok = false;
     if (!ok) break;
-    // per-solve step, status and next time step (one thread per solve)
-    if (gid < nsolves) {
-      volatile BatchSolve* b = &ctx.bs[gid];
-      if (!b->done) {
-        const double tn = b->t + b->dt;
-        b->t = tn;
-        b->nsteps = b->nsteps + 1;
-        const double mn = __longlong_as_double((long long)atomicAdd(&ctx.bs[gid].lam_min_bits, 0ull));
-        double dtn = cfl * mn;
-        int done = 0;
-        if (b->failed) done = 1;
-        else if (tn >= b->T * (1.0 - 1e-14)) done = 1;
-        else if (tn + dtn > b->T) dtn = b->T - tn;
-        b->dt = dtn;
-        b->done = done;
-        atomicExch(&ctx.bs[gid].lam_min_bits, dbits(dinf()));
-        if (!done) atomicAdd(&ctl->active[slot], 1u);
-      }
-    }
-    if (gid == 0) {
-      atomicExch(&ctl->active[slot ^ 1], 0u);
-      atomicAdd(&ctl->steps_run, 1);
-    }
+    batch_finish_step(ctx.bs, ctl, gid, nsolves, cfl, slot);
     if (!grid_barrier(ctl, spin_limit, false)) { ok = false; break; }
     if (*(volatile unsigned*)&ctl->active[slot] == 0) break;
   }
   if (!ok && threadIdx.x == 0) atomicOr(&ctl->flags, 2u);
+}
+
+// The batched step as three launches (schedule launch_mode 1): the same
+// phases as k_batch without grid barriers, each kernel at its own register
+// budget and occupancy; the launches of many steps are captured in one graph.
+template <typename R, int EQ, bool LIM>
+__global__ void __launch_bounds__(LIM ? kThreads : kLeanThreads) k_batch_recon(
+    const __grid_constant__ CUtensorMap mGeo, const __grid_constant__ CUtensorMap mIdx, R* __restrict__ Pb, EqParams P,
+    BatchCtx<R> ctx) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + recon_smem_bytes<R, EQ>() - 128 - 2 * sizeof(uint64_t));
+  if (threadIdx.x == 0) {
+    prefetch_tensormap(&mGeo); prefetch_tensormap(&mIdx);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph[2] = {0u, 0u};
+  recon_phase<R, EQ, LIM, LIM ? kThreads : kLeanThreads>(ctx, &mGeo, &mIdx, P, Pb, base, bar, ph);
+}
+
+template <typename R, int EQ, bool LIM>
+__global__ void __launch_bounds__(kThreads, edge_min_blocks<R, EQ>()) k_batch_edge(
+    const __grid_constant__ CUtensorMap mEgeo, const __grid_constant__ CUtensorMap mIdx,
+    const __grid_constant__ CUtensorMap mLgeo, R* __restrict__ Pb, EqParams P, BatchCtx<R> ctx) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_base(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + edge_smem_bytes<R, EQ>() - 128 - 2 * sizeof(uint64_t));
+  if (threadIdx.x == 0) {
+    prefetch_tensormap(&mEgeo); prefetch_tensormap(&mIdx);
+    if (LIM) prefetch_tensormap(&mLgeo);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned ph[2] = {0u, 0u};
+  edge_phase<R, EQ, false, LIM>(ctx, &mEgeo, &mIdx, &mLgeo, P, Pb, base, bar, ph);
+}
+
+__global__ void k_batch_finish(BatchSolve* bs, BatchCtl* ctl, int nsolves, double cfl, int slot) {
+  batch_finish_step(bs, ctl, blockIdx.x * blockDim.x + threadIdx.x, nsolves, cfl, slot);
 }
 
 // CFL step of the current state (after an upload or a change of target).
@@ -1785,6 +1836,42 @@ cudaError_t launch_batch(int prec, int eq, const BatchArgs& a, cudaStream_t st) 
   if (eq == 0) return launch_batch_t<float, 0, false>(a, st);
   if (eq == 1) return launch_batch_t<float, 1, false>(a, st);
   return lim ? launch_batch_t<float, 2, true>(a, st) : launch_batch_t<float, 2, false>(a, st);
+}
+
+namespace {
+template <typename R, int EQ, bool LIM> int batch_recon_cap() {
+  static const int cap = resident_blocks(k_batch_recon<R, EQ, LIM>, LIM ? kThreads : kLeanThreads,
+                                         recon_smem_bytes<R, EQ>());
+  return cap;
+}
+template <typename R, int EQ, bool LIM> int batch_edge_cap() {
+  static const int cap = resident_blocks(k_batch_edge<R, EQ, LIM>, kThreads, edge_smem_bytes<R, EQ>());
+  return cap;
+}
+template <typename R, int EQ, bool LIM> cudaError_t launch_batch_step_t(const BatchArgs& a, int slot, cudaStream_t st) {
+  BatchCtx<R> ctx{a.tiles, a.ntiles, reinterpret_cast<R*>(a.C), a.bs, a.ctl, reinterpret_cast<R*>(a.U0),
+                  reinterpret_cast<R*>(a.U1)};
+  const int nt = a.ntiles > 0 ? a.ntiles : 1;
+  const int rc = batch_recon_cap<R, EQ, LIM>(), ec = batch_edge_cap<R, EQ, LIM>();
+  k_batch_recon<R, EQ, LIM><<<nt < rc ? nt : rc, LIM ? kThreads : kLeanThreads, recon_smem_bytes<R, EQ>(), st>>>(
+      a.maps->geo, a.maps->idx, reinterpret_cast<R*>(a.Pb), a.P, ctx);
+  k_batch_edge<R, EQ, LIM><<<nt < ec ? nt : ec, kThreads, edge_smem_bytes<R, EQ>(), st>>>(
+      a.maps->egeo, a.maps->idx, a.maps->lgeo, reinterpret_cast<R*>(a.Pb), a.P, ctx);
+  k_batch_finish<<<(a.nsolves + 127) / 128, 128, 0, st>>>(a.bs, a.ctl, a.nsolves, a.cfl, slot);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_batch_step(int prec, int eq, const BatchArgs& a, int slot, cudaStream_t st) {
+  const bool lim = eq == 2 && a.P.positivity;
+  if (prec == 0) {
+    if (eq == 0) return launch_batch_step_t<double, 0, false>(a, slot, st);
+    if (eq == 1) return launch_batch_step_t<double, 1, false>(a, slot, st);
+    return lim ? launch_batch_step_t<double, 2, true>(a, slot, st) : launch_batch_step_t<double, 2, false>(a, slot, st);
+  }
+  if (eq == 0) return launch_batch_step_t<float, 0, false>(a, slot, st);
+  if (eq == 1) return launch_batch_step_t<float, 1, false>(a, slot, st);
+  return lim ? launch_batch_step_t<float, 2, true>(a, slot, st) : launch_batch_step_t<float, 2, false>(a, slot, st);
 }
 
 void launch_batch_cfl(int prec, int eq, const BatchArgs& a, cudaStream_t st) {

@@ -143,6 +143,9 @@ void launch_adjoint(int prec, const AdjointArgs& a, cudaStream_t st);
 // Resident blocks per SM of the batched kernel (cooperative launch limit).
 int batch_blocks_per_sm(int prec, int eq, bool lim);
 cudaError_t launch_batch(int prec, int eq, const BatchArgs& a, cudaStream_t st);
+// One batched step as three launches (reconstruction, flux/update, per-solve
+// finish); slot: the step's parity for the running-solve counts.
+cudaError_t launch_batch_step(int prec, int eq, const BatchArgs& a, int slot, cudaStream_t st);
 void launch_batch_cfl(int prec, int eq, const BatchArgs& a, cudaStream_t st);
 void launch_batch_dt(BatchSolve* bs, int n, double cfl, double T, int has_T, cudaStream_t st);
 void launch_batch_reset_ctl(BatchCtl* ctl, cudaStream_t st);

@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("tile_order", ctypes.c_int32),
                 ("steps_per_launch", ctypes.c_int32), ("withhold_block", ctypes.c_int32),
-                ("spin_limit", ctypes.c_int64)]
+                ("spin_limit", ctypes.c_int64), ("launch_mode", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -162,3 +162,37 @@ def test_batch_is_deterministic():
         outs.append([b.get_state(k)[0] for k in range(3)])
     for k in range(3):
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_three_launch_form_equals_persistent_form(precision):
+    """launch_mode 1 (three launches per step in a graph) runs the same phases
+    as the persistent cooperative launch: every solve's state, time and step
+    count agree bit for bit, with the scale limiter and flux blending, through
+    run_to (chunks, tail compaction) and a fixed number of steps."""
+    meshes, states = riemann_batch([6, 11, 4, 15, 9, 7], 100)
+    out = {}
+    for mode in (0, 1):
+        b = hweno.Batch(meshes, states, eq="euler", precision=precision, positivity=True)
+        b.set_schedule(launch_mode=mode, tile_order=2)
+        assert b.schedule()["launch_mode"] == mode
+        b.run_to(0.05)
+        b.steps(5)
+        out[mode] = [b.get_state(k) for k in range(len(meshes))]
+        b.close()
+    for k in range(len(meshes)):
+        (U0, t0, n0, f0), (U1, t1, n1, f1) = out[0][k], out[1][k]
+        assert (t0, n0, f0) == (t1, n1, f1), k
+        assert np.array_equal(U0, U1), (k, np.abs(U0 - U1).max())
+
+
+def test_autotune_considers_both_launch_forms():
+    meshes, states = riemann_batch([5, 9, 7], 200)
+    b = hweno.Batch(meshes, states, eq="euler", precision="fp32", positivity=True)
+    best = b.autotune(trial_steps=4)
+    assert best["launch_mode"] in (0, 1) and best["trial_ms"] > 0
+    b.set_schedule(launch_mode=1, withhold_block=-1)
+    with pytest.raises(hweno.HwError) as e:
+        b.set_schedule(launch_mode=1, withhold_block=0)
+    assert e.value.status == hweno.HW_EINVAL
+    b.close()
