@@ -64,11 +64,11 @@ def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
 # dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
 # it was measured on; it is reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources_sha": "673d9969c2939909",
+    "sources_sha": "7074c0e683641011",
     # full-size (1,999,928-cell) single-pass ncu capture, per cell; FP64 with
     # the edge-once flux phase (its two kernels)
-    "per_cell": {"recon_fp32": 633.5, "edge_fp32": 467.2,
-                 "recon_fp64": 1276.7, "edge_flux_fp64": 954.2, "edge_update_fp64": 471.8},
+    "per_cell": {"recon_fp32": 633.5, "edge_fp32": 467.1,
+                 "recon_fp64": 1276.8, "edge_flux_fp64": 954.2, "edge_update_fp64": 471.7},
 }
 
 # Floating-point operations per cell and launch (FMA counted as 2), from the
