@@ -14,6 +14,15 @@
 //             timeflux, taylor2dtime); the CFL step of the next step.  In
 //             FP32 the update of the average is a compensated sum (one FP32
 //             compensation word per cell and component).
+//   k_edge_flux, k_edge_update: the same flux phase with every edge
+//             evaluated once, by its left cell, into a per-point buffer, then
+//             the update of every cell from its own or its neighbour's slots
+//             (bit for bit k_edge's result; the FP64 default).
+//   k_batch : many solves in one persistent cooperative launch (grid
+//             barriers between the phases); k_batch_recon, k_batch_edge,
+//             k_batch_finish: the same step as three launches.
+//   k_fused : reconstruction and flux of a tile and its halo in one kernel
+//             (option).
 //   k_cfl, k_consv, k_scatter_state, k_gather_state: CFL step of a state,
 //             FP64 conservation sums, host-order <-> internal-order copies.
 //
