@@ -165,63 +165,96 @@ __device__ __forceinline__ void nonlinear_weights(float Wave, const float beta[4
 }
 
 // ---------------------------------------------------------------- reconstruction
-// Steps 1-6 of Section 2.2 for component c of cell i: returns the combined
-// quadratic (Eq. recon) as monomials in the scaled frame of the cell,
+// Steps 1-6 of Section 2.2 for NC components of cell i: returns each
+// component's combined quadratic (Eq. recon) as monomials in the scaled frame
+// of the cell,
 //   q(xi, eta) = q0 + q1 xi + q2 eta + q3 xi^2 + q4 xi eta + q5 eta^2.
-// GA: accessor of this cell's geometry planes, ga(p) = plane p (see RGeo).
-// W0, V0, Y0: the cell's averages; Wl, Vl, Yl: those of the stencil members
-// K1..K3 (a boundary ghost carries the cell's own values).
+// GA: accessor of this cell's geometry planes, ga(p) = plane p (see RGeo);
+// each plane is read once for the NC components, whose arithmetic is that of
+// one component, term by term.  W0, V0, Y0: the cell's averages; Wl, Vl, Yl:
+// those of the stencil members K1..K3 (a boundary ghost carries the cell's
+// own values).
+template <typename R, int NC, typename GA>
+__device__ __forceinline__ void reconstruct_components(const GA& ga, const R* W0, const R* V0, const R* Y0,
+                                                       const R (*Wl)[3], const R (*Vl)[3], const R (*Yl)[3],
+                                                       const EqParams& P, R (*q)[6]) {
+  // Step 1: constrained least squares solved once on the host; here the operator
+  R rhs[NC][9];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const R w = ga(G_W + l);
+#pragma unroll
+    for (int n = 0; n < NC; ++n) {
+      rhs[n][l] = Wl[n][l] - W0[n];
+      rhs[n][3 + 2 * l] = V0[n] + w * (Vl[n][l] - V0[n]);
+      rhs[n][4 + 2 * l] = Y0[n] + w * (Yl[n][l] - Y0[n]);
+    }
+  }
+  R cc[NC][5];
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    R s[NC];
+#pragma unroll
+    for (int n = 0; n < NC; ++n) s[n] = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const R g = ga(G_M1 + r * 9 + k);
+#pragma unroll
+      for (int n = 0; n < NC; ++n) s[n] += g * rhs[n][k];
+    }
+#pragma unroll
+    for (int n = 0; n < NC; ++n) cc[n][r] = s[n];
+  }
+  // Step 2: linear polynomials on {K0, K_l}
+  R b[NC][3][2];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const R g0 = ga(G_P + l * 6 + r * 3 + 0), g1 = ga(G_P + l * 6 + r * 3 + 1), g2 = ga(G_P + l * 6 + r * 3 + 2);
+#pragma unroll
+      for (int n = 0; n < NC; ++n) b[n][l][r] = g0 * (Wl[n][l] - W0[n]) + g1 * Vl[n][l] + g2 * Yl[n][l];
+    }
+  const R m3 = ga(G_MOM), m4 = ga(G_MOM + 1), m5 = ga(G_MOM + 2);
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    // Step 4 (Eq. smoo1): in the frame scaled by h0 = sqrt|K0| the factors
+    // |K0|^|s| cancel the chain-rule factors, leaving the scaled derivatives.
+    R beta[4];
+    beta[0] = cc[n][0] * cc[n][0] + cc[n][1] * cc[n][1] + R(4) * cc[n][2] * cc[n][2] + cc[n][3] * cc[n][3] +
+              R(4) * cc[n][4] * cc[n][4];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) beta[l + 1] = b[n][l][0] * b[n][l][0] + b[n][l][1] * b[n][l][1];
+    // Step 5
+    const R Wave = (W0[n] + Wl[n][0] + Wl[n][1] + Wl[n][2]) * R(0.25) + R(1e-30);
+    R om[4];
+    nonlinear_weights(Wave, beta, P, om);
+    // Step 6: q = (om1/g1) p1 + sum_l (om_l - om1 g_l / g1) p_l
+    const R a1 = om[0] / EqC<R>::g(P, 0);
+    R al[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) al[l] = om[l + 1] - a1 * EqC<R>::g(P, l + 1);
+    R q1 = a1 * cc[n][0], q2 = a1 * cc[n][1];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) { q1 += al[l] * b[n][l][0]; q2 += al[l] * b[n][l][1]; }
+    const R q3 = a1 * cc[n][2], q4 = a1 * cc[n][3], q5 = a1 * cc[n][4];
+    // the constant parts of p1..p4 all equal Wbar_0 and the coefficients sum to one
+    q[n][0] = W0[n] - q3 * m3 - q4 * m4 - q5 * m5;
+    q[n][1] = q1; q[n][2] = q2; q[n][3] = q3; q[n][4] = q4; q[n][5] = q5;
+  }
+}
+
+// One component (the same arithmetic).
 template <typename R, typename GA>
 __device__ __forceinline__ void reconstruct_component(const GA& ga, const R W0, const R V0, const R Y0,
                                                       const R Wl[3], const R Vl[3], const R Yl[3],
                                                       const EqParams& P, R q[6]) {
-  // Step 1: constrained least squares solved once on the host; here the operator
-  R rhs[9];
+  R wl[1][3], vl[1][3], yl[1][3], qq[1][6];
 #pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    rhs[l] = Wl[l] - W0;
-    const R w = ga(G_W + l);
-    rhs[3 + 2 * l] = V0 + w * (Vl[l] - V0);
-    rhs[4 + 2 * l] = Y0 + w * (Yl[l] - Y0);
-  }
-  R cc[5];
+  for (int l = 0; l < 3; ++l) { wl[0][l] = Wl[l]; vl[0][l] = Vl[l]; yl[0][l] = Yl[l]; }
+  reconstruct_components<R, 1>(ga, &W0, &V0, &Y0, wl, vl, yl, P, qq);
 #pragma unroll
-  for (int r = 0; r < 5; ++r) {
-    R s = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s += ga(G_M1 + r * 9 + k) * rhs[k];
-    cc[r] = s;
-  }
-  // Step 2: linear polynomials on {K0, K_l}
-  R b[3][2];
-#pragma unroll
-  for (int l = 0; l < 3; ++l)
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-      b[l][r] = ga(G_P + l * 6 + r * 3 + 0) * (Wl[l] - W0) + ga(G_P + l * 6 + r * 3 + 1) * Vl[l] +
-                ga(G_P + l * 6 + r * 3 + 2) * Yl[l];
-  // Step 4 (Eq. smoo1): in the frame scaled by h0 = sqrt|K0| the factors
-  // |K0|^|s| cancel the chain-rule factors, leaving the scaled derivatives.
-  R beta[4];
-  beta[0] = cc[0] * cc[0] + cc[1] * cc[1] + R(4) * cc[2] * cc[2] + cc[3] * cc[3] + R(4) * cc[4] * cc[4];
-#pragma unroll
-  for (int l = 0; l < 3; ++l) beta[l + 1] = b[l][0] * b[l][0] + b[l][1] * b[l][1];
-  // Step 5
-  const R Wave = (W0 + Wl[0] + Wl[1] + Wl[2]) * R(0.25) + R(1e-30);
-  R om[4];
-  nonlinear_weights(Wave, beta, P, om);
-  // Step 6: q = (om1/g1) p1 + sum_l (om_l - om1 g_l / g1) p_l
-  const R a1 = om[0] / EqC<R>::g(P, 0);
-  R al[3];
-#pragma unroll
-  for (int l = 0; l < 3; ++l) al[l] = om[l + 1] - a1 * EqC<R>::g(P, l + 1);
-  R q1 = a1 * cc[0], q2 = a1 * cc[1];
-#pragma unroll
-  for (int l = 0; l < 3; ++l) { q1 += al[l] * b[l][0]; q2 += al[l] * b[l][1]; }
-  const R q3 = a1 * cc[2], q4 = a1 * cc[3], q5 = a1 * cc[4];
-  // the constant parts of p1..p4 all equal Wbar_0 and the coefficients sum to one
-  q[0] = W0 - q3 * ga(G_MOM) - q4 * ga(G_MOM + 1) - q5 * ga(G_MOM + 2);
-  q[1] = q1; q[2] = q2; q[3] = q3; q[4] = q4; q[5] = q5;
+  for (int k = 0; k < 6; ++k) q[k] = qq[0][k];
 }
 
 // ---------------------------------------------------------------- Lax-Wendroff

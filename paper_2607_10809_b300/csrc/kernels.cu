@@ -267,30 +267,43 @@ __device__ __forceinline__ void recon_lw_block(const Src& src, int count, const 
   constexpr int m = EqTraits<EQ>::m;
   static_assert(!LIM || NT == 6 * kCells, "the limiter path takes one thread per (cell, point)");
   const int t = threadIdx.x;
-  for (int task = t; task < m * kCells; task += NT) {
-    const int lc = task % kCells, c = task / kCells;
+  // phase A: NC components of a cell per task (two with 2 threads per cell, so
+  // that the cell's geometry planes are read once for both)
+  constexpr int NC = (NT == 2 * kCells && m % 2 == 0) ? 2 : 1;
+  for (int task = t; task < (m / NC) * kCells; task += NT) {
+    const int lc = task % kCells, c0 = (task / kCells) * NC;
     if (lc < count) {
-      R Wl[3], Vl[3], Yl[3];
+      R W0[NC], V0[NC], Y0[NC], Wl[NC][3], Vl[NC][3], Yl[NC][3];
       const R* own = src.own(lc);
+#pragma unroll
+      for (int n = 0; n < NC; ++n) { W0[n] = own[c0 + n]; V0[n] = own[m + c0 + n]; Y0[n] = own[2 * m + c0 + n]; }
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int nb = src.nbr(j, lc);
         if (nb >= 0) {
           const R* rec = U + (size_t)nb * 3 * m;
-          Wl[j] = rec[0 * m + c]; Vl[j] = rec[1 * m + c]; Yl[j] = rec[2 * m + c];
+#pragma unroll
+          for (int n = 0; n < NC; ++n) {
+            Wl[n][j] = rec[0 * m + c0 + n]; Vl[n][j] = rec[1 * m + c0 + n]; Yl[n][j] = rec[2 * m + c0 + n];
+          }
         } else {
           // boundary ghost: outward unit normal of edge j from the scaled vertices
           const int jn = (j + 1) % 3;
           const R dx = src.geo(G_VX + 2 * jn, lc) - src.geo(G_VX + 2 * j, lc);
           const R dy = src.geo(G_VX + 2 * jn + 1, lc) - src.geo(G_VX + 2 * j + 1, lc);
           const R il = R(1) / sqrt(dx * dx + dy * dy);
-          ghost_component<R, EQ>(ghost_type(src.nbe(lc), j), own, dy * il, -dx * il, c, P, Wl[j], Vl[j], Yl[j]);
+#pragma unroll
+          for (int n = 0; n < NC; ++n)
+            ghost_component<R, EQ>(ghost_type(src.nbe(lc), j), own, dy * il, -dx * il, c0 + n, P, Wl[n][j],
+                                   Vl[n][j], Yl[n][j]);
         }
       }
-      R q[6];
-      reconstruct_component<R>(src.geo_of(lc), own[0 * m + c], own[1 * m + c], own[2 * m + c], Wl, Vl, Yl, P, q);
+      R q[NC][6];
+      reconstruct_components<R, NC>(src.geo_of(lc), W0, V0, Y0, Wl, Vl, Yl, P, q);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) qs[c][k][lc] = q[k];
+      for (int n = 0; n < NC; ++n)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) qs[c0 + n][k][lc] = q[n][k];
     }
   }
   __syncthreads();
