@@ -64,18 +64,18 @@ def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
 # dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
 # it was measured on; it is reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources_sha": "7074c0e683641011",
+    "sources_sha": "35911a42b720bcef",
     # full-size (1,999,928-cell) single-pass ncu capture, per cell; FP64 with
     # the edge-once flux phase (its two kernels)
-    "per_cell": {"recon_fp32": 633.5, "edge_fp32": 467.1,
-                 "recon_fp64": 1276.8, "edge_flux_fp64": 954.2, "edge_update_fp64": 471.7},
+    "per_cell": {"recon_fp32": 633.1, "edge_fp32": 467.2,
+                 "recon_fp64": 1275.9, "edge_flux_fp64": 954.2, "edge_update_fp64": 471.7},
 }
 
 # Floating-point operations per cell and launch (FMA counted as 2), from the
 # executed-instruction counters of one ncu capture of the 499,942-cell vortex in
 # FP64 (smsp__sass_thread_inst_executed_op_d{fma,add,mul}_pred_on.sum / cells),
 # valid for the sources hash of TRAFFIC.
-FLOPS = {"recon_fp64": 4382, "edge_fp64": 1227 + 256}   # edge: k_edge_flux + k_edge_update
+FLOPS = {"recon_fp64": 4376, "edge_fp64": 1227 + 256}   # edge: k_edge_flux + k_edge_update
 
 # FP64 peak of the B300 per SM clock: the nominal 1.25 TFLOP/s at the 2032 MHz
 # maximum clock is 2 FP64 FMA per SM per clock on 148 SMs (a one-off FMA probe
