@@ -1,6 +1,7 @@
 """The single-mesh partition with a per-step halo exchange (host logic), on CPU:
 the CPU oracle stands in for each rank's GPU solver.  Partitioned runs, in
-one process and on two gloo ranks, must reproduce the single-process run to
+one process and on two gloo ranks (host-array exchange, and the device path's
+row exchange with CPU tensors), must reproduce the single-process run to
 1e-12; the batch split must balance the solves."""
 import os
 import socket
@@ -37,6 +38,37 @@ class OracleStepper:
 
     def set(self, U, t):
         self.U = np.ascontiguousarray(U)
+
+
+class OracleRowStepper(OracleStepper):
+    """The device stepper's interface (halo rows handed over as tensors, the
+    dt minimum as a tensor all-reduce) played by the oracle on CPU tensors, so
+    that the NCCL path's exchange logic runs over gloo."""
+
+    def __init__(self, mesh, U, part, **kw):
+        import torch
+        super().__init__(mesh, U, **kw)
+        self.m = self.U.shape[1]
+        self.width = 3 * self.m
+        self.dtype = torch.float64
+        self.device = torch.device("cpu")
+        self.send_rows = {q: torch.from_numpy(np.asarray(idx, dtype=np.int64)) for q, idx in part.send.items()}
+        self.recv_rows = {q: torch.from_numpy(np.asarray(idx, dtype=np.int64)) for q, idx in part.recv.items()}
+
+    def export(self):
+        pass
+
+    def outgoing(self, q):
+        import torch
+        idx = self.send_rows[q].numpy()
+        return torch.from_numpy(np.ascontiguousarray(self.U[:, :, idx].reshape(self.width, idx.size).T))
+
+    def incoming(self, q, data):
+        idx = self.recv_rows[q].numpy()
+        self.U[:, :, idx] = data.numpy().T.reshape(3, self.m, idx.size)
+
+    def commit(self, t):
+        pass
 
 
 def cases():
@@ -124,6 +156,34 @@ def test_partition_on_two_gloo_ranks_matches_the_single_run(case):
     ref = single_run(mesh, U0, kw, nsteps)
     out = mp.Manager().dict()
     mp.spawn(_worker, args=(world, _free_port(), case, nsteps, out), nprocs=world, join=True)
+    parts = PT.build(mesh, order_of(mesh), world)
+    U = PT.gather_state(parts, [out[r][0] for r in range(world)], mesh.nt)
+    assert abs(out[0][1] - out[1][1]) == 0.0
+    assert rel_linf(U, ref) < TOL
+
+
+def _worker_rows(rank, world, port, case, nsteps, out):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        mesh, U0, kw = cases()[case]
+        parts = PT.build(mesh, order_of(mesh), world)
+        p = parts[rank]
+        st = OracleRowStepper(p.mesh, PT.scatter_state(U0, p), p, **kw)
+        t = PT.run_distributed_device(p, st, nsteps)
+        out[rank] = (st.get(), t)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("case", ["vortex-periodic", "lax-walls-inflow"])
+def test_row_exchange_path_on_two_gloo_ranks_matches_the_single_run(case):
+    """run_distributed_device (halo rows as tensors, isend / irecv, dt by a
+    tensor all-reduce) over gloo with CPU tensors."""
+    world, nsteps = 2, 5
+    mesh, U0, kw = cases()[case]
+    ref = single_run(mesh, U0, kw, nsteps)
+    out = mp.Manager().dict()
+    mp.spawn(_worker_rows, args=(world, _free_port(), case, nsteps, out), nprocs=world, join=True)
     parts = PT.build(mesh, order_of(mesh), world)
     U = PT.gather_state(parts, [out[r][0] for r in range(world)], mesh.nt)
     assert abs(out[0][1] - out[1][1]) == 0.0
