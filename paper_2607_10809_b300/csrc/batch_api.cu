@@ -433,12 +433,26 @@ hw_status hw_batch_steps(hw_batch* b, int32_t steps, double* ms) {
   hw::NvtxRange nvtx_("hw_batch_steps");
   if (!b || steps <= 0) return bfail(HW_EINVAL, "bad arguments");
   launch_batch_dt(b->bs(), b->n, b->opt.cfl, 1e300, 1, b->stream);
-  if (hw_status st = capture_graph(b, steps)) return st;
+  // the three-launch form captures at most kCompactChunk steps per graph (three
+  // nodes per step); longer runs replay it, reading the flags in between (each
+  // replay starts by clearing them)
+  const int chunk = b->sched.launch_mode == 1 ? std::min<int>(steps, kCompactChunk) : steps;
+  if (hw_status st = capture_graph(b, chunk)) return st;
   cudaEvent_t e0, e1;
   HB_CUDA(cudaEventCreate(&e0));
   HB_CUDA(cudaEventCreate(&e1));
+  unsigned flags = 0u;
   HB_CUDA(cudaEventRecord(e0, b->stream));
-  HB_CUDA(cudaGraphLaunch(b->graph, b->stream));
+  for (int done = 0; done < steps;) {
+    const int n = std::min(chunk, steps - done);
+    if (hw_status st = capture_graph(b, n)) return st;   // the chunk, or the last, shorter one
+    HB_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    done += n;
+    if (done < steps) {
+      if (hw_status st = read_status(b)) return st;
+      flags |= b->h_ctl->flags;
+    }
+  }
   HB_CUDA(cudaEventRecord(e1, b->stream));
   HB_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;
@@ -447,7 +461,8 @@ hw_status hw_batch_steps(hw_batch* b, int32_t steps, double* ms) {
   cudaEventDestroy(e1);
   if (ms) *ms = t;
   if (hw_status st = read_status(b)) return st;
-  if (b->h_ctl->flags & 2u) return bfail(HW_ETIMEOUT, "batched kernel: a bounded wait gave up");
+  flags |= b->h_ctl->flags;
+  if (flags & 2u) return bfail(HW_ETIMEOUT, "batched kernel: a bounded wait gave up");
   return HW_OK;
 }
 

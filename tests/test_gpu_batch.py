@@ -172,7 +172,8 @@ def test_three_launch_form_equals_persistent_form(precision):
     """launch_mode 1 (three launches per step in a graph) runs the same phases
     as the persistent cooperative launch: every solve's state, time and step
     count agree bit for bit, with the scale limiter and flux blending, through
-    run_to (chunks, tail compaction) and a fixed number of steps."""
+    run_to (chunks, tail compaction) and a fixed number of steps longer than
+    one captured graph."""
     meshes, states = riemann_batch([6, 11, 4, 15, 9, 7], 100)
     out = {}
     for mode in (0, 1):
@@ -180,7 +181,7 @@ def test_three_launch_form_equals_persistent_form(precision):
         b.set_schedule(launch_mode=mode, tile_order=2)
         assert b.schedule()["launch_mode"] == mode
         b.run_to(0.05)
-        b.steps(5)
+        b.steps(300)   # the three-launch form replays a graph of at most 128 steps
         out[mode] = [b.get_state(k) for k in range(len(meshes))]
         b.close()
     for k in range(len(meshes)):
