@@ -42,6 +42,8 @@
 // vector loads (mostly L2 hits thanks to the Hilbert order).
 #include <cuda.h>
 
+#include <type_traits>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -255,6 +257,23 @@ template <typename R, int EQ> struct GlobalCells {
   __device__ __forceinline__ GlobalGeo<R> geo_of(int lc) const { return GlobalGeo<R>{rg, ld, cells[lc]}; }
 };
 
+// Components c0 .. c0 + NC - 1 of the three fields (Wbar, Vbar, Ybar) of a
+// state record with m components; a pair (c0 even, the record 16-byte aligned)
+// in one 8- or 16-byte load per field.
+template <typename R, int NC>
+__device__ __forceinline__ void load_fields(const R* rec, int m, int c0, R* w, R* v, R* y) {
+  if constexpr (NC == 2) {
+    using V2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const V2 a = *reinterpret_cast<const V2*>(rec + c0);
+    const V2 b = *reinterpret_cast<const V2*>(rec + m + c0);
+    const V2 c = *reinterpret_cast<const V2*>(rec + 2 * m + c0);
+    w[0] = a.x; w[1] = a.y; v[0] = b.x; v[1] = b.y; y[0] = c.x; y[1] = c.y;
+  } else {
+#pragma unroll
+    for (int n = 0; n < NC; ++n) { w[n] = rec[c0 + n]; v[n] = rec[m + c0 + n]; y[n] = rec[2 * m + c0 + n]; }
+  }
+}
+
 // Reconstruction (Steps 1-6) and the Lax-Wendroff procedure at the six edge
 // Gauss points of up to kCells cells.  NT: threads of the block; phase A runs
 // the (cell, component) tasks and phase B the (cell, point) tasks in passes of
@@ -275,17 +294,15 @@ __device__ __forceinline__ void recon_lw_block(const Src& src, int count, const 
     if (lc < count) {
       R W0[NC], V0[NC], Y0[NC], Wl[NC][3], Vl[NC][3], Yl[NC][3];
       const R* own = src.own(lc);
-#pragma unroll
-      for (int n = 0; n < NC; ++n) { W0[n] = own[c0 + n]; V0[n] = own[m + c0 + n]; Y0[n] = own[2 * m + c0 + n]; }
+      load_fields<R, NC>(own, m, c0, W0, V0, Y0);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int nb = src.nbr(j, lc);
         if (nb >= 0) {
-          const R* rec = U + (size_t)nb * 3 * m;
+          R w[NC], v[NC], y[NC];
+          load_fields<R, NC>(U + (size_t)nb * 3 * m, m, c0, w, v, y);
 #pragma unroll
-          for (int n = 0; n < NC; ++n) {
-            Wl[n][j] = rec[0 * m + c0 + n]; Vl[n][j] = rec[1 * m + c0 + n]; Yl[n][j] = rec[2 * m + c0 + n];
-          }
+          for (int n = 0; n < NC; ++n) { Wl[n][j] = w[n]; Vl[n][j] = v[n]; Yl[n][j] = y[n]; }
         } else {
           // boundary ghost: outward unit normal of edge j from the scaled vertices
           const int jn = (j + 1) % 3;
