@@ -64,11 +64,11 @@ def alg_bytes(kernel: str, s: int, m: int = 4) -> int:
 # dram__bytes_write.sum per launch / cells) and the hash of the kernel sources
 # it was measured on; it is reported only while the sources are unchanged.
 TRAFFIC = {
-    "sources_sha": "35911a42b720bcef",
+    "sources_sha": "2378e78abc0a979f",
     # full-size (1,999,928-cell) single-pass ncu capture, per cell; FP64 with
     # the edge-once flux phase (its two kernels)
-    "per_cell": {"recon_fp32": 633.1, "edge_fp32": 467.2,
-                 "recon_fp64": 1275.9, "edge_flux_fp64": 954.2, "edge_update_fp64": 471.7},
+    "per_cell": {"recon_fp32": 632.9, "edge_fp32": 467.1,
+                 "recon_fp64": 1275.7, "edge_flux_fp64": 954.1, "edge_update_fp64": 471.9},
 }
 
 # Floating-point operations per cell and launch (FMA counted as 2), from the
