@@ -288,7 +288,13 @@ hw_status hw_mesh_create(const double* xy, int64_t nvert, const int32_t* tri, in
   if (bc != HW_BC_PERIODIC && bc != HW_BC_TRANSMISSIVE) return fail(HW_EINVAL, "unknown boundary condition");
   hw_mesh* h = new (std::nothrow) hw_mesh();
   if (!h) return fail(HW_ENOMEM, "host allocation failed");
-  std::string err = build_mesh(xy, nvert, tri, ntri, Lx, Ly, bc, h->M);
+  std::string err;
+  try {
+    err = build_mesh(xy, nvert, tri, ntri, Lx, Ly, bc, h->M);
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return fail(HW_ENOMEM, "host allocation failed while building the mesh");
+  }
   if (!err.empty()) {
     delete h;
     const bool inval = err.find("out of range") != std::string::npos || err.find("needs") != std::string::npos;

@@ -1,16 +1,72 @@
-// Host FP64 precompute for the HWENO library: connectivity (hash matching of
-// edge keys), Hilbert renumbering, and per-cell reconstruction operators of
-// Section 2.2 (Steps 1 and 2) with the edge geometry of Eqs. fx and derave2d2.
+// Host FP64 precompute for the HWENO library: connectivity (half-edges
+// grouped by their smaller vertex), Hilbert renumbering, and per-cell
+// reconstruction operators of Section 2.2 (Steps 1 and 2) with the edge
+// geometry of Eqs. fx and derave2d2.  The per-cell passes run on the host's
+// cores; every value is computed by the same arithmetic whatever the thread
+// count, so the result is bit for bit that of one thread.
+#include <sched.h>
+
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
-#include <unordered_map>
+#include <system_error>
+#include <thread>
 
 #include "internal.h"
 
 namespace hw {
 namespace {
+
+// Host threads for the precompute: the CPUs this process may run on (at most 64).
+int host_threads() {
+  cpu_set_t set;
+  if (sched_getaffinity(0, sizeof(set), &set) == 0) {
+    const int n = CPU_COUNT(&set);
+    if (n > 0) return std::min(n, 64);
+  }
+  const unsigned n = std::thread::hardware_concurrency();
+  return n ? (int)std::min(n, 64u) : 1;
+}
+
+// fn(begin, end) over consecutive ranges that cover [0, n), each on its own
+// thread (the caller runs the first, and any range whose thread could not be
+// started).  fn must write only outputs owned by its indices.
+template <class F>
+void parallel_ranges(int64_t n, const F& fn) {
+  constexpr int64_t kGrain = 8192;
+  const int nw = (int)std::min<int64_t>(host_threads(), (n + kGrain - 1) / kGrain);
+  if (nw <= 1) {
+    if (n > 0) fn(int64_t(0), n);
+    return;
+  }
+  auto lo = [n, nw](int w) { return n * w / nw; };
+  std::vector<std::thread> pool;
+  int w = 1;
+  try {
+    pool.reserve((size_t)nw - 1);
+    for (; w < nw; ++w) pool.emplace_back([&fn, &lo, w] { fn(lo(w), lo(w + 1)); });
+  } catch (const std::exception&) {
+    // fewer threads than ranges: the caller takes the rest below
+  }
+  fn(lo(0), lo(1));
+  for (int r = w; r < nw; ++r) fn(lo(r), lo(r + 1));
+  for (auto& t : pool) t.join();
+}
+
+// The error a one-thread pass would meet first: every range reports its own
+// first failing index, and the lowest index over all ranges wins.
+struct FirstError {
+  std::mutex mu;
+  int64_t at = LLONG_MAX;
+  const char* msg = nullptr;
+  void report(int64_t i, const char* m) {
+    std::lock_guard<std::mutex> g(mu);
+    if (i < at) { at = i; msg = m; }
+  }
+};
 
 // Hilbert index of (x, y) on an n x n grid, n = 2^order: walk the quadrants
 // from the coarsest level, accumulating the quadrant rank and rotating /
@@ -84,74 +140,124 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
     if (tri[i] < 0 || tri[i] >= nv) return "vertex index out of range";
   if (bc == 0 && (Lx <= 0 || Ly <= 0)) return "periodic boundary needs Lx > 0 and Ly > 0";
 
-  // ---- connectivity by hashing the sorted vertex pair of every edge
+  // ---- connectivity: the half-edges (3t + j, from vertex j to vertex j+1 of
+  // triangle t) grouped by their smaller vertex with a counting sort, then by
+  // their larger vertex inside each group; two half-edges with the same vertex
+  // pair are one interior edge.  A fault is reported at the half-edge where a
+  // scan in triangle order would first see it: a repeated vertex at that
+  // half-edge, a triangle meeting itself at the second half-edge of a pair, a
+  // non-manifold edge at the third.
   M.nbr_orig.assign(3 * nt, -1);
   M.nbe_orig.assign(3 * nt, -1);
   {
-    std::unordered_map<uint64_t, int64_t> open;
-    open.reserve(3 * nt / 2 + 16);
-    for (int64_t t = 0; t < nt; ++t)
-      for (int j = 0; j < 3; ++j) {
-        uint32_t a = (uint32_t)tri[3 * t + j], b = (uint32_t)tri[3 * t + (j + 1) % 3];
-        if (a == b) return "degenerate triangle";
-        uint64_t key = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
-        auto it = open.find(key);
-        if (it == open.end()) {
-          open.emplace(key, 3 * t + j);
-        } else {
-          int64_t o = it->second;
-          if (o < 0) return "non-manifold edge (shared by more than two triangles)";
-          int64_t u = o / 3; int ju = (int)(o % 3);
-          if (u == t) return "triangle is its own neighbour (mesh too coarse for its period)";
-          M.nbr_orig[3 * t + j] = (int32_t)u; M.nbe_orig[3 * t + j] = ju;
-          M.nbr_orig[3 * u + ju] = (int32_t)t; M.nbe_orig[3 * u + ju] = j;
-          it->second = -1;
-        }
+    const int64_t nh = 3 * nt;
+    int64_t fault_at = LLONG_MAX;
+    const char* fault = nullptr;
+    auto note = [&](int64_t h, const char* msg) {
+      if (h < fault_at) { fault_at = h; fault = msg; }
+    };
+    std::vector<int64_t> first((size_t)nv + 1, 0);
+    for (int64_t h = 0; h < nh; ++h) {
+      const int32_t a = tri[h], b = tri[h - h % 3 + (h % 3 + 1) % 3];
+      if (a == b) note(h, "degenerate triangle");
+      else ++first[(size_t)std::min(a, b) + 1];
+    }
+    for (int64_t v = 0; v < nv; ++v) first[(size_t)v + 1] += first[(size_t)v];
+    // entries of a group in ascending half-edge order: (larger vertex, half-edge)
+    std::vector<std::pair<int32_t, int64_t>> ent((size_t)first[(size_t)nv]);
+    {
+      std::vector<int64_t> fill(first.begin(), first.end() - 1);
+      for (int64_t h = 0; h < nh; ++h) {
+        const int32_t a = tri[h], b = tri[h - h % 3 + (h % 3 + 1) % 3];
+        if (a != b) ent[(size_t)fill[(size_t)std::min(a, b)]++] = {std::max(a, b), h};
       }
+    }
+    for (int64_t v = 0; v < nv; ++v) {
+      auto* g0 = ent.data() + first[(size_t)v];
+      auto* g1 = ent.data() + first[(size_t)v + 1];
+      std::sort(g0, g1);   // by larger vertex, then by half-edge
+      for (auto* r = g0; r < g1;) {
+        auto* e = r + 1;
+        while (e < g1 && e->first == r->first) ++e;
+        if (e - r >= 3) note(r[2].second, "non-manifold edge (shared by more than two triangles)");
+        if (e - r >= 2) {
+          const int64_t h1 = r[0].second, h2 = r[1].second;
+          const int64_t t1 = h1 / 3, t2 = h2 / 3;
+          if (t1 == t2) {
+            note(h2, "triangle is its own neighbour (mesh too coarse for its period)");
+          } else {
+            M.nbr_orig[h2] = (int32_t)t1; M.nbe_orig[h2] = (int32_t)(h1 % 3);
+            M.nbr_orig[h1] = (int32_t)t2; M.nbe_orig[h1] = (int32_t)(h2 % 3);
+          }
+        }
+        r = e;
+      }
+    }
+    if (fault) return fault;
     if (bc == 0)
-      for (int64_t i = 0; i < 3 * nt; ++i)
+      for (int64_t i = 0; i < nh; ++i)
         if (M.nbr_orig[i] < 0) return "open edge on a periodic mesh";
   }
 
   // ---- unwrapped vertex coordinates, areas, barycenters
   std::vector<double> VX(3 * nt), VY(3 * nt), A(nt), CX(nt), CY(nt);
-  auto near = [](double d, double L) { return L > 0 ? d - L * std::nearbyint(d / L) : d; };
-  for (int64_t t = 0; t < nt; ++t) {
-    const double x0 = xy[2 * tri[3 * t]], y0 = xy[2 * tri[3 * t] + 1];
-    for (int v = 0; v < 3; ++v) {
-      VX[3 * t + v] = x0 + near(xy[2 * tri[3 * t + v]] - x0, Lx);
-      VY[3 * t + v] = y0 + near(xy[2 * tri[3 * t + v] + 1] - y0, Ly);
-    }
-    const double* X = &VX[3 * t]; const double* Y = &VY[3 * t];
-    A[t] = 0.5 * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
-    if (!(A[t] > 0)) return "triangle not counter-clockwise or degenerate";
-    CX[t] = (X[0] + X[1] + X[2]) / 3.0;
-    CY[t] = (Y[0] + Y[1] + Y[2]) / 3.0;
+  {
+    auto near = [](double d, double L) { return L > 0 ? d - L * std::nearbyint(d / L) : d; };
+    FirstError fe;
+    parallel_ranges(nt, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        const double x0 = xy[2 * tri[3 * t]], y0 = xy[2 * tri[3 * t] + 1];
+        for (int v = 0; v < 3; ++v) {
+          VX[3 * t + v] = x0 + near(xy[2 * tri[3 * t + v]] - x0, Lx);
+          VY[3 * t + v] = y0 + near(xy[2 * tri[3 * t + v] + 1] - y0, Ly);
+        }
+        const double* X = &VX[3 * t]; const double* Y = &VY[3 * t];
+        A[t] = 0.5 * ((X[1] - X[0]) * (Y[2] - Y[0]) - (X[2] - X[0]) * (Y[1] - Y[0]));
+        if (!(A[t] > 0)) { fe.report(t, "triangle not counter-clockwise or degenerate"); return; }
+        CX[t] = (X[0] + X[1] + X[2]) / 3.0;
+        CY[t] = (Y[0] + Y[1] + Y[2]) / 3.0;
+      }
+    });
+    if (fe.msg) return fe.msg;
   }
 
-  // ---- Hilbert renumbering of the barycenters
+  // ---- Hilbert renumbering of the barycenters (sorted by key, ties by the
+  // caller's index)
   {
-    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
     std::vector<double> bx(nt), by(nt);
-    for (int64_t t = 0; t < nt; ++t) {
-      bx[t] = Lx > 0 ? CX[t] - Lx * std::floor(CX[t] / Lx) : CX[t];
-      by[t] = Ly > 0 ? CY[t] - Ly * std::floor(CY[t] / Ly) : CY[t];
-      x0 = std::min(x0, bx[t]); x1 = std::max(x1, bx[t]);
-      y0 = std::min(y0, by[t]); y1 = std::max(y1, by[t]);
-    }
-    const int order = 16;
+    std::mutex mu;
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    parallel_ranges(nt, [&](int64_t t0, int64_t t1) {
+      double lx0 = 1e300, lx1 = -1e300, ly0 = 1e300, ly1 = -1e300;
+      for (int64_t t = t0; t < t1; ++t) {
+        bx[t] = Lx > 0 ? CX[t] - Lx * std::floor(CX[t] / Lx) : CX[t];
+        by[t] = Ly > 0 ? CY[t] - Ly * std::floor(CY[t] / Ly) : CY[t];
+        lx0 = std::min(lx0, bx[t]); lx1 = std::max(lx1, bx[t]);
+        ly0 = std::min(ly0, by[t]); ly1 = std::max(ly1, by[t]);
+      }
+      std::lock_guard<std::mutex> g(mu);
+      x0 = std::min(x0, lx0); x1 = std::max(x1, lx1);
+      y0 = std::min(y0, ly0); y1 = std::max(y1, ly1);
+    });
+    const int order = 16;   // keys below 4^16 = 2^32
     const double span = std::max(x1 - x0, y1 - y0) * (1 + 1e-12) + 1e-300;
-    std::vector<uint64_t> key(nt);
-    for (int64_t t = 0; t < nt; ++t) {
-      uint32_t ix = (uint32_t)std::min(65535.0, std::floor((bx[t] - x0) / span * 65536.0));
-      uint32_t iy = (uint32_t)std::min(65535.0, std::floor((by[t] - y0) / span * 65536.0));
-      key[t] = hilbert_key(ix, iy, order);
-    }
+    std::vector<uint64_t> key(nt);   // Hilbert key in the high word, caller's index in the low word
+    parallel_ranges(nt, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        uint32_t ix = (uint32_t)std::min(65535.0, std::floor((bx[t] - x0) / span * 65536.0));
+        uint32_t iy = (uint32_t)std::min(65535.0, std::floor((by[t] - y0) / span * 65536.0));
+        key[t] = (hilbert_key(ix, iy, order) << 32) | (uint64_t)t;
+      }
+    });
+    std::sort(key.begin(), key.end());
     M.perm.resize(nt);
-    std::iota(M.perm.begin(), M.perm.end(), 0);
-    std::stable_sort(M.perm.begin(), M.perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
     M.inv.resize(nt);
-    for (int64_t k = 0; k < nt; ++k) M.inv[M.perm[k]] = (int32_t)k;
+    parallel_ranges(nt, [&](int64_t k0, int64_t k1) {
+      for (int64_t k = k0; k < k1; ++k) M.perm[k] = (int32_t)(key[k] & 0xffffffffu);
+    });
+    parallel_ranges(nt, [&](int64_t k0, int64_t k1) {
+      for (int64_t k = k0; k < k1; ++k) M.inv[M.perm[k]] = (int32_t)k;
+    });
   }
 
   // ---- per-cell operators, internal order
@@ -160,7 +266,9 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
   M.area.resize(nt);
   auto R = [&](int p, int64_t k) -> double& { return M.rgeo[(size_t)p * nt + k]; };
   auto I = [&](int p, int64_t k) -> int32_t& { return M.igeo[(size_t)p * nt + k]; };
-  for (int64_t k = 0; k < nt; ++k) {
+  FirstError fe;
+  parallel_ranges(nt, [&](int64_t k0, int64_t k1) {
+  for (int64_t k = k0; k < k1; ++k) {
     const int64_t t = M.perm[k];
     const double A0 = A[t], h0 = std::sqrt(A0), ih = 1.0 / h0;
     M.area[k] = A0;
@@ -224,7 +332,7 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
     householder_qr_5x3(a, Q, Rr);
     double rmax = 0, rmin = 1e300;
     for (int i = 0; i < 3; ++i) { rmax = std::max(rmax, std::fabs(Rr[i][i])); rmin = std::min(rmin, std::fabs(Rr[i][i])); }
-    if (!(rmin > 1e-10 * rmax)) return "ill-conditioned stencil (cell-average constraints)";
+    if (!(rmin > 1e-10 * rmax)) { fe.report(k, "ill-conditioned stencil (cell-average constraints)"); return; }
     // P0 = Q1 R1^{-T}  (5x3): solve R1^T y = e_i for unit e_i
     double Rinvt[3][3];
     for (int i = 0; i < 3; ++i) {
@@ -256,7 +364,10 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
     for (int r = 0; r < 6; ++r)
       for (int i = 0; i < 2; ++i) for (int j2 = 0; j2 < 2; ++j2) HtH[i][j2] += H[r][i] * H[r][j2];
     const double det = HtH[0][0] * HtH[1][1] - HtH[0][1] * HtH[1][0];
-    if (!(det > 1e-12 * (HtH[0][0] * HtH[1][1] + 1e-300))) return "ill-conditioned stencil (least-squares rows)";
+    if (!(det > 1e-12 * (HtH[0][0] * HtH[1][1] + 1e-300))) {
+      fe.report(k, "ill-conditioned stencil (least-squares rows)");
+      return;
+    }
     const double G[2][2] = {{HtH[1][1] / det, -HtH[0][1] / det}, {-HtH[1][0] / det, HtH[0][0] / det}};
     // K = N G H^T  (5x6)
     double Kd[5][6];
@@ -298,25 +409,31 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
         }
     }
   }
+  });
+  if (fe.msg) return fe.msg;
 
   // ---- perimeter / area of each cell and of its neighbours (one FP64 value per
   // cell, so that both cells of an edge see the same numbers)
   {
     std::vector<double> pk(nt);
-    for (int64_t t = 0; t < nt; ++t) {
-      double per = 0;
-      for (int j = 0; j < 3; ++j)
-        per += std::hypot(VX[3 * t + (j + 1) % 3] - VX[3 * t + j], VY[3 * t + (j + 1) % 3] - VY[3 * t + j]);
-      pk[t] = per / A[t];
-    }
-    for (int64_t k = 0; k < nt; ++k) {
-      const int64_t t = M.perm[k];
-      R(G_PK, k) = pk[t];
-      for (int j = 0; j < 3; ++j) {
-        const int32_t u = M.nbr_orig[3 * t + j];
-        R(G_PN + j, k) = u >= 0 ? pk[u] : pk[t];
+    parallel_ranges(nt, [&](int64_t t0, int64_t t1) {
+      for (int64_t t = t0; t < t1; ++t) {
+        double per = 0;
+        for (int j = 0; j < 3; ++j)
+          per += std::hypot(VX[3 * t + (j + 1) % 3] - VX[3 * t + j], VY[3 * t + (j + 1) % 3] - VY[3 * t + j]);
+        pk[t] = per / A[t];
       }
-    }
+    });
+    parallel_ranges(nt, [&](int64_t k0, int64_t k1) {
+      for (int64_t k = k0; k < k1; ++k) {
+        const int64_t t = M.perm[k];
+        R(G_PK, k) = pk[t];
+        for (int j = 0; j < 3; ++j) {
+          const int32_t u = M.nbr_orig[3 * t + j];
+          R(G_PN + j, k) = u >= 0 ? pk[u] : pk[t];
+        }
+      }
+    });
   }
 
   // ---- edge geometry: canonical normal, outward of the edge's owner, the
@@ -324,7 +441,8 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
   // owner's frame: every edge gets one normal and one length whatever the
   // renumbering (on a periodic seam the two cells' frames differ by a shift
   // that is not exact in floating point)
-  for (int64_t k = 0; k < nt; ++k) {
+  parallel_ranges(nt, [&](int64_t k0, int64_t k1) {
+  for (int64_t k = k0; k < k1; ++k) {
     const int64_t t = M.perm[k];
     for (int j = 0; j < 3; ++j) {
       const int32_t un = I(I_NBR + j, k);
@@ -339,6 +457,7 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
       R(G_EL + j, k) = len / A[t];
     }
   }
+  });
   return "";
 }
 

@@ -162,3 +162,53 @@ def test_linear_weights_must_be_positive_and_sum_to_one(lib, weights, why):
     assert e.value.status == hweno.HW_EINVAL, why
     assert "linear weight" in str(e.value)
     hweno.hw_workspace_bytes(m.h, hweno.options("advection", gamma_lin=(0.7, 0.1, 0.1, 0.1)), "fp64")
+
+
+def test_connectivity_bit_exact_against_oracle_on_a_mesh_split_over_threads(lib):
+    """A mesh large enough that the precompute splits its passes into many
+    ranges over the host's cores: connectivity still equals the oracle's."""
+    mesh = I.jittered_periodic(160, 10.0, seed=6)   # 51,200 triangles
+    m = hweno.Mesh(mesh)
+    nbr, nbe = m.neighbors()
+    onbr, onbe = oracle.Oracle(mesh).neighbors()
+    np.testing.assert_array_equal(nbr, onbr)
+    np.testing.assert_array_equal(nbe, onbe)
+
+
+_ONE_CPU_CHILD = r"""
+import os, sys, hashlib
+os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+sys.path.insert(0, sys.argv[1])
+from paper_2607_10809_b300 import hweno, inputs as I
+m = hweno.Mesh(I.jittered_periodic(160, 10.0, seed=6))
+nbr, nbe = m.neighbors()
+print(hashlib.sha256(nbr.tobytes() + nbe.tobytes() + m.permutation().tobytes()).hexdigest())
+"""
+
+
+def test_mesh_precompute_does_not_depend_on_the_thread_count(lib):
+    """The host precompute runs its passes on the CPUs the process may use;
+    restricted to one CPU it gives the same neighbours and Hilbert order."""
+    import hashlib
+    import subprocess
+    import sys
+    if len(os.sched_getaffinity(0)) < 2:
+        pytest.skip("one CPU available: nothing to compare")
+    m = hweno.Mesh(I.jittered_periodic(160, 10.0, seed=6))
+    nbr, nbe = m.neighbors()
+    here = hashlib.sha256(nbr.tobytes() + nbe.tobytes() + m.permutation().tobytes()).hexdigest()
+    out = subprocess.run([sys.executable, "-c", _ONE_CPU_CHILD, ROOT], capture_output=True, text=True, check=True)
+    assert out.stdout.strip() == here
+
+
+def test_mesh_faults_are_reported_in_triangle_order(lib):
+    """With two faults, the message is the one a scan of the triangles in the
+    caller's order meets first."""
+    mesh = I.jittered_periodic(4, 1.0, seed=1)
+    degen = mesh.tri.copy(); degen[2, 1] = degen[2, 0]
+    a = np.concatenate([degen, mesh.tri[:1]])                  # repeated vertex first, duplicate last
+    b = np.concatenate([mesh.tri[:1], mesh.tri[:1], degen])    # duplicate first, repeated vertex later
+    with pytest.raises(hweno.HwError, match="degenerate"):
+        hweno.hw_mesh_create(mesh.xy, a, 1.0, 1.0, 0)
+    with pytest.raises(hweno.HwError, match="non-manifold"):
+        hweno.hw_mesh_create(mesh.xy, b, 1.0, 1.0, 0)
