@@ -2,7 +2,7 @@
 // array: the halo exchange of a partitioned mesh moves only the cells another
 // part holds, not the whole state.  A row is the cell's record (Wbar, Vbar,
 // Ybar: 3m values) and, in FP32, its m compensation words.  A row index
-// outside [0, N) is skipped and raises bit 4 of the flags word.
+// outside [0, N) is skipped and raises bit 2 (value 4) of the flags word.
 #include <cuda_runtime.h>
 
 #include <cstdint>
