@@ -97,7 +97,13 @@ def build(mesh: I.Mesh, order: np.ndarray, nparts: int) -> list:
         cells = np.union1d(own, np.union1d(ring1, ring2))
         local = I.Mesh(xy=mesh.xy, tri=mesh.tri[cells], Lx=mesh.Lx, Ly=mesh.Ly, bc=1)
         if mesh.edge_bc is not None:
-            local.edge_bc = mesh.edge_bc[cells].copy()
+            # an edge to a cell outside the part is on the local mesh's outer
+            # rim: open (transmissive) there, whatever the caller's array holds
+            # for that edge, which is interior to the whole mesh
+            ebc = np.array(mesh.edge_bc[cells], dtype=np.int32)
+            nb = nbr[cells]
+            ebc[(nb >= 0) & ~np.isin(nb, cells)] = I.BC_TRANSMISSIVE
+            local.edge_bc = ebc
         # keep only the vertices the local cells use
         used = np.unique(local.tri)
         remap = -np.ones(mesh.nv, dtype=np.int64)

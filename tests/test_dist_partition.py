@@ -118,6 +118,25 @@ def test_partition_tables():
         assert np.array_equal(np.sort(got), np.nonzero(~p.owned)[0])
 
 
+def test_partition_rim_edges_are_open_whatever_the_interior_edge_types():
+    """Boundary types are read only on boundary edges, so the caller may leave
+    anything at interior edges; the parts' outer rims are boundary edges of
+    their local meshes and must come out transmissive, not the caller's value."""
+    mesh, U0, kw = cases()["lax-walls-inflow"]
+    nbr = PT.neighbours(mesh)
+    mesh.edge_bc = np.where(nbr >= 0, 0, mesh.edge_bc).astype(np.int32)   # 0: not a boundary type
+    nsteps = 4
+    ref = single_run(mesh, U0, kw, nsteps)
+    parts = PT.build(mesh, order_of(mesh), 3)
+    for p in parts:
+        lnbr = PT.neighbours(p.mesh)
+        assert np.isin(p.mesh.edge_bc[lnbr < 0], (I.BC_TRANSMISSIVE, I.BC_REFLECTIVE, I.BC_INFLOW)).all()
+    steppers = [OracleStepper(p.mesh, PT.scatter_state(U0, p), **kw) for p in parts]
+    PT.run_local(parts, steppers, nsteps)
+    U = PT.gather_state(parts, [s.get() for s in steppers], mesh.nt)
+    assert rel_linf(U, ref) < TOL
+
+
 @pytest.mark.parametrize("case", ["vortex-periodic", "lax-walls-inflow"])
 def test_partition_in_one_process_matches_the_single_run(case):
     mesh, U0, kw = cases()[case]
