@@ -172,27 +172,37 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
         if (a != b) ent[(size_t)fill[(size_t)std::min(a, b)]++] = {std::max(a, b), h};
       }
     }
-    for (int64_t v = 0; v < nv; ++v) {
-      auto* g0 = ent.data() + first[(size_t)v];
-      auto* g1 = ent.data() + first[(size_t)v + 1];
-      std::sort(g0, g1);   // by larger vertex, then by half-edge
-      for (auto* r = g0; r < g1;) {
-        auto* e = r + 1;
-        while (e < g1 && e->first == r->first) ++e;
-        if (e - r >= 3) note(r[2].second, "non-manifold edge (shared by more than two triangles)");
-        if (e - r >= 2) {
-          const int64_t h1 = r[0].second, h2 = r[1].second;
-          const int64_t t1 = h1 / 3, t2 = h2 / 3;
-          if (t1 == t2) {
-            note(h2, "triangle is its own neighbour (mesh too coarse for its period)");
-          } else {
-            M.nbr_orig[h2] = (int32_t)t1; M.nbe_orig[h2] = (int32_t)(h1 % 3);
-            M.nbr_orig[h1] = (int32_t)t2; M.nbe_orig[h1] = (int32_t)(h2 % 3);
+    FirstError fe;   // the groups hold half-edges in any order: each range keeps its lowest fault
+    parallel_ranges(nv, [&](int64_t v0, int64_t v1) {
+      int64_t at = LLONG_MAX;
+      const char* msg = nullptr;
+      auto note_here = [&](int64_t h, const char* m) {
+        if (h < at) { at = h; msg = m; }
+      };
+      for (int64_t v = v0; v < v1; ++v) {
+        auto* g0 = ent.data() + first[(size_t)v];
+        auto* g1 = ent.data() + first[(size_t)v + 1];
+        std::sort(g0, g1);   // by larger vertex, then by half-edge
+        for (auto* r = g0; r < g1;) {
+          auto* e = r + 1;
+          while (e < g1 && e->first == r->first) ++e;
+          if (e - r >= 3) note_here(r[2].second, "non-manifold edge (shared by more than two triangles)");
+          if (e - r >= 2) {
+            const int64_t h1 = r[0].second, h2 = r[1].second;
+            const int64_t t1 = h1 / 3, t2 = h2 / 3;
+            if (t1 == t2) {
+              note_here(h2, "triangle is its own neighbour (mesh too coarse for its period)");
+            } else {
+              M.nbr_orig[h2] = (int32_t)t1; M.nbe_orig[h2] = (int32_t)(h1 % 3);
+              M.nbr_orig[h1] = (int32_t)t2; M.nbe_orig[h1] = (int32_t)(h2 % 3);
+            }
           }
+          r = e;
         }
-        r = e;
       }
-    }
+      if (msg) fe.report(at, msg);
+    });
+    if (fe.msg) note(fe.at, fe.msg);
     if (fault) return fault;
     if (bc == 0)
       for (int64_t i = 0; i < nh; ++i)
