@@ -5,6 +5,7 @@
 // cores; every value is computed by the same arithmetic whatever the thread
 // count, so the result is bit for bit that of one thread.
 #include <sched.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <climits>
@@ -271,6 +272,16 @@ std::string build_mesh(const double* xy, int64_t nv, const int32_t* tri, int64_t
   }
 
   // ---- per-cell operators, internal order
+  {
+    // the largest host array (90 doubles per cell): ask for huge pages before
+    // its first touch, which halves the time of the fill below (advice only)
+    const size_t n = (size_t)NRGEO * nt;
+    M.rgeo.reserve(n);
+    const uintptr_t huge = uintptr_t(1) << 21;
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(M.rgeo.data()) + huge - 1) & ~(huge - 1);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(M.rgeo.data()) + n * sizeof(double)) & ~(huge - 1);
+    if (e > a) madvise(reinterpret_cast<void*>(a), e - a, MADV_HUGEPAGE);
+  }
   M.rgeo.assign((size_t)NRGEO * nt, 0.0);
   M.igeo.assign((size_t)NIGEO * nt, -1);
   M.area.resize(nt);
