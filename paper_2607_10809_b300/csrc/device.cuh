@@ -18,7 +18,7 @@ struct DevScalars {
   double cfl;
   unsigned long long lam_min_bits;   // min_K inradius/lambda as the bits of a positive double
   unsigned int counter;              // blocks done (last-block finalisation)
-  unsigned int flags;                // bit 0: non-finite / non-physical, bit 1: spin limit
+  unsigned int flags;                // bit 0: non-finite / non-physical, bit 1: spin limit, bit 2: a state row index out of range
   long long nsteps;                  // steps taken
   int done;                          // target reached
   int has_T;
