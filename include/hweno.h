@@ -211,7 +211,10 @@ hw_status hw_solver_destroy(hw_solver* s);
 
 /* Same as hw_step, but the scratch of the step (the edge-point buffer between
  * the reconstruction and the flux kernels) is a static device array inside the
- * library instead of part of the workspace.  The paper has no counterpart: it
+ * library instead of part of the workspace (the per-point flux buffer of the
+ * edge-once flux phase, step_kernels 3 and the FP64 default, stays in the
+ * workspace; the fused kernel of step_kernels 2 is not used here, the step
+ * runs the separate kernels).  The paper has no counterpart: it
  * is for callers that cannot call cudaMalloc (hosts that own the device memory
  * pool, plug-ins handed fixed buffers, runtimes that must not allocate while
  * running); they still pass the state and geometry through the solver's

@@ -659,11 +659,12 @@ hw_status hw_solver_destroy(hw_solver* s) {
 // Some callers cannot call cudaMalloc at all: code running inside a host that
 // owns the device memory pool and forbids other allocators, plug-ins that are
 // handed fixed buffers, or runtimes that must not allocate once they are
-// running.  For them the edge-point buffer (the only scratch of a step: the
-// Taylor data written by the reconstruction kernel and read back by the flux
-// kernel) lives in the file-scope device array below instead of in the
-// workspace.  Every GPU that loads this library holds the array until the
-// process exits.
+// running.  For them the edge-point buffer (the Taylor data written by the
+// reconstruction kernel and read back by the flux kernels, the largest scratch
+// of a step) lives in the file-scope device array below instead of in the
+// workspace; the per-point flux buffer of the edge-once flux phase stays in
+// the workspace the caller passed at hw_state_init.  Every GPU that loads this
+// library holds the array until the process exits.
 namespace {
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
