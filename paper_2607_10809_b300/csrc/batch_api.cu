@@ -438,9 +438,16 @@ hw_status hw_batch_steps(hw_batch* b, int32_t steps, double* ms) {
   // replay starts by clearing them)
   const int chunk = b->sched.launch_mode == 1 ? std::min<int>(steps, kCompactChunk) : steps;
   if (hw_status st = capture_graph(b, chunk)) return st;
-  cudaEvent_t e0, e1;
-  HB_CUDA(cudaEventCreate(&e0));
-  HB_CUDA(cudaEventCreate(&e1));
+  struct Events {   // destroyed on every return path
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Events() {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } ev;
+  HB_CUDA(cudaEventCreate(&ev.e0));
+  HB_CUDA(cudaEventCreate(&ev.e1));
+  cudaEvent_t e0 = ev.e0, e1 = ev.e1;
   unsigned flags = 0u;
   HB_CUDA(cudaEventRecord(e0, b->stream));
   for (int done = 0; done < steps;) {
@@ -457,8 +464,6 @@ hw_status hw_batch_steps(hw_batch* b, int32_t steps, double* ms) {
   HB_CUDA(cudaEventSynchronize(e1));
   float t = 0.f;
   cudaEventElapsedTime(&t, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (ms) *ms = t;
   if (hw_status st = read_status(b)) return st;
   flags |= b->h_ctl->flags;
